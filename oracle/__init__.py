@@ -1,0 +1,332 @@
+"""CPU FP64 oracle for the rank-k eigen-update of Oh & Hu (arXiv 1706.00773).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package.  The product library
+never imports, links or calls it, and it imports nothing from the product.  The
+only module both sides share is ``workloads`` (seeded input generators).
+
+Plain and slow on purpose.  The C part (``orc.c``) holds the Jacobi
+eigensolver, the root count, the bisection root finder and the eq. (10)
+vectors.  This module composes them with numpy library primitives (matmul).
+Each function names the passage of the paper it follows.  The paper prints no
+worked example, so every pin is a closed form, an invariant, a special case or
+a library routine (``tests/test_oracle_pins.py``).
+
+Conventions: Q is n x n with eigenvectors as columns (column-major in memory
+when handed to C), lam is ascending, K is n x k, sigma holds +1/-1 per column.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "orc.c")
+_SO = os.path.join(_HERE, "_orc.so")
+_lock = threading.Lock()
+_lib = None
+
+EPS = float(np.finfo(np.float64).eps)
+FLAG_CAP = 1
+FLAG_AT_POLE = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile orc.c into oracle/_orc.so with gcc (plain -O2, IEEE semantics)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _bind(path: str):
+    """Load a compiled oracle library and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    d, i64, i32, i8 = (ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int8))
+    lib.orc_jacobi.argtypes = [ctypes.c_int, d, d, d, ctypes.c_int]
+    lib.orc_jacobi.restype = ctypes.c_int
+    lib.orc_count.argtypes = [ctypes.c_int64, ctypes.c_int, d, d, i8, ctypes.c_int64, ctypes.c_double]
+    lib.orc_count.restype = ctypes.c_int64
+    lib.orc_pole_count.argtypes = [ctypes.c_int64, ctypes.c_int, d, d, i8, ctypes.c_int64]
+    lib.orc_pole_count.restype = ctypes.c_int64
+    lib.orc_roots.argtypes = [ctypes.c_int64, ctypes.c_int, d, d, i8, ctypes.c_int64, i64,
+                              ctypes.c_int, i64, d, d, i32, i32]
+    lib.orc_roots.restype = ctypes.c_int
+    lib.orc_vectors.argtypes = [ctypes.c_int64, ctypes.c_int, d, d, i8, ctypes.c_int64, i64, d,
+                                i32, d, d]
+    lib.orc_vectors.restype = ctypes.c_int
+    return lib
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(_SO)
+        return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _colmajor(A):
+    return np.asfortranarray(np.asarray(A, dtype=np.float64))
+
+
+def _sig(sigma, k):
+    if sigma is None:
+        return np.ones(k, dtype=np.int8)
+    s = np.asarray(sigma).astype(np.int8).reshape(-1)
+    if s.shape[0] != k or not np.all(np.abs(s) == 1):
+        raise ValueError("sigma must hold k entries of +1/-1")
+    return np.ascontiguousarray(s)
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------------------
+# Plain definitions
+# ---------------------------------------------------------------------------
+def jacobi_eig(A, vectors: bool = True, max_sweeps: int = 60):
+    """Cyclic Jacobi eigendecomposition of a symmetric matrix (textbook definition).
+
+    Returns (w ascending, V with eigenvectors as columns or None)."""
+    A = _colmajor(A).copy(order="F")
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n), order="F") if vectors else None
+    rc = _L().orc_jacobi(n, _p(A, ctypes.c_double), _p(w, ctypes.c_double),
+                         _p(V, ctypes.c_double) if vectors else None, max_sweeps)
+    if rc < 0:
+        raise ValueError("orc_jacobi failed")
+    return w, V
+
+
+def updated_matrix(Q, lam, K, sigma=None):
+    """A' = Q diag(lam) Q^T + K diag(sigma) K^T (Sec. 2.1 problem statement)."""
+    Q = np.asarray(Q, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64).reshape(Q.shape[0], -1)
+    s = _sig(sigma, K.shape[1]).astype(np.float64)
+    A = (Q * np.asarray(lam, dtype=np.float64)[None, :]) @ Q.T + (K * s[None, :]) @ K.T
+    return 0.5 * (A + A.T)
+
+
+def dense_update(Q, lam, K, sigma=None, vectors: bool = True):
+    """The direct EVD comparison system (Sec. 3): Jacobi on the dense A'.  n <= ~512."""
+    A = updated_matrix(Q, lam, K, sigma)
+    return jacobi_eig(A, vectors=vectors)
+
+
+# ---------------------------------------------------------------------------
+# Method steps, in the paper's order
+# ---------------------------------------------------------------------------
+def project(Q, K):
+    """U = Q^T K (Sec. 2.1, below eq. (1)); numpy matmul as the library step."""
+    return np.asarray(Q, dtype=np.float64).T @ np.asarray(K, dtype=np.float64).reshape(Q.shape[0], -1)
+
+
+def rank2_perturbation(n: int, j: int, a):
+    """Sec. 2.2 Steps 1-2: e_j a^T + a e_j^T = (x y) [[0,1],[1,0]] (x y)^T with x = e_j, y = a.
+    The 2x2 middle matrix is S diag(1,-1) S^T, S = [[1,1],[1,-1]]/sqrt(2), so
+    (u1 u2) = (x y) S: K = [(e_j + a)/sqrt2, (e_j - a)/sqrt2], sigma = (+1, -1)."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    if a.shape[0] != n or not (0 <= j < n):
+        raise ValueError("bad rank-2 arguments")
+    e = np.zeros(n)
+    e[j] = 1.0
+    r = 1.0 / np.sqrt(2.0)
+    K = np.stack([(e + a) * r, (e - a) * r], axis=1)
+    return K, np.array([1, -1], dtype=np.int8)
+
+
+def deflation_mask(lam, U):
+    """Rows u_i small enough to drop (the paper assumes all u_i != 0 and
+    distinct lam, Sec. 2.1; it is silent on what to do otherwise).
+    Row i is deflated when |u_i|_2 |U|_F <= 8 eps (max|lam| + |U|_F^2): zeroing it
+    changes A' by at most that much in norm.  Deflated pairs keep mu = lam_i
+    and the old eigenvector q_i."""
+    lam = np.asarray(lam, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64).reshape(lam.shape[0], -1)
+    rown = np.sqrt(np.sum(U * U, axis=1))
+    fro2 = float(np.sum(U * U))
+    fro = np.sqrt(fro2)
+    tol = 8.0 * EPS * (float(np.max(np.abs(lam))) + fro2)
+    return rown * fro <= tol
+
+
+def count(lam, U, sigma, x: float, origin: int = -1) -> int:
+    """#{mu < x} for diag(lam) + U Sigma U^T (the root-count sub-problem, Sec. 2.1-2.2).
+    With origin >= 0 the point is x = lam[origin] + x."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    U = _colmajor(U)
+    n, k = U.shape
+    s = _sig(sigma, k)
+    return int(_L().orc_count(n, k, _p(lam, ctypes.c_double), _p(U, ctypes.c_double),
+                              _p(s, ctypes.c_int8), origin, float(x)))
+
+
+def pole_count(lam, U, sigma, p: int) -> int:
+    """#{mu < lam_p}: the count at a pole (limit from the left)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    U = _colmajor(U)
+    n, k = U.shape
+    s = _sig(sigma, k)
+    return int(_L().orc_pole_count(n, k, _p(lam, ctypes.c_double), _p(U, ctypes.c_double),
+                                   _p(s, ctypes.c_int8), int(p)))
+
+
+def roots(lam, U, sigma=None, sel=None, nthreads: int | None = None):
+    """Roots of f (Sec. 2.3, bisection on the count inside interlacing brackets)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    U = _colmajor(U)
+    n, k = U.shape
+    s = _sig(sigma, k)
+    if sel is None:
+        m = n
+        selp = None
+    else:
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        m = sel.shape[0]
+        selp = _p(sel, ctypes.c_int64)
+    origin = np.zeros(m, dtype=np.int64)
+    tau = np.zeros(m)
+    mu = np.zeros(m)
+    iters = np.zeros(m, dtype=np.int32)
+    flags = np.zeros(m, dtype=np.int32)
+    if m == 0:
+        return dict(origin=origin, tau=tau, mu=mu, iters=iters, flags=flags)
+    rc = _L().orc_roots(n, k, _p(lam, ctypes.c_double), _p(U, ctypes.c_double), _p(s, ctypes.c_int8),
+                        m, selp, int(nthreads or default_threads()), _p(origin, ctypes.c_int64),
+                        _p(tau, ctypes.c_double), _p(mu, ctypes.c_double), _p(iters, ctypes.c_int32),
+                        _p(flags, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("orc_roots failed (%d)" % rc)
+    return dict(origin=origin, tau=tau, mu=mu, iters=iters, flags=flags)
+
+
+def tie_ranks(mu, lam_scale: float):
+    """Rank of each root inside a run of numerically equal roots (repeated eigenvalue)."""
+    mu = np.asarray(mu)
+    rank = np.zeros(mu.shape[0], dtype=np.int32)
+    tol = 64.0 * EPS * max(lam_scale, 1e-300)
+    for i in range(1, mu.shape[0]):
+        if mu[i] - mu[i - 1] <= tol:
+            rank[i] = rank[i - 1] + 1
+    return rank
+
+
+def vectors(lam, U, sigma, origin, tau, rank=None):
+    """Eq. (10) in the old eigenbasis: columns w_s (unit, largest entry positive)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    U = _colmajor(U)
+    n, k = U.shape
+    s = _sig(sigma, k)
+    origin = np.ascontiguousarray(origin, dtype=np.int64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    m = origin.shape[0]
+    rk = np.ascontiguousarray(rank if rank is not None else np.zeros(m), dtype=np.int32)
+    W = np.zeros((n, m), order="F")
+    if m:
+        rc = _L().orc_vectors(n, k, _p(lam, ctypes.c_double), _p(U, ctypes.c_double),
+                              _p(s, ctypes.c_int8), m, _p(origin, ctypes.c_int64),
+                              _p(tau, ctypes.c_double), _p(rk, ctypes.c_int32),
+                              _p(W, ctypes.c_double), None)
+        if rc != 0:
+            raise ValueError("orc_vectors failed")
+    # A repeated root gives a multi-dimensional eigenspace; eq. (10) maps an
+    # orthonormal basis of the k x k null space onto a basis of it that need not
+    # be orthonormal, so orthonormalise inside each run of equal roots.
+    i = 0
+    while i < m:
+        j = i + 1
+        while j < m and rk[j] > 0:
+            j += 1
+        if j - i > 1:
+            Qg, _ = np.linalg.qr(W[:, i:j])
+            W[:, i:j] = Qg
+        i = j
+    return W
+
+
+def update(Q, lam, K, sigma=None, want_vectors: bool = True, sel=None, nthreads: int | None = None):
+    """The whole update A' = Q diag(lam) Q^T + K Sigma K^T, by the paper's method.
+
+    sel (optional) lists root indices m of the non-deflated sub-problem to solve
+    (sampling for large n); then only those roots and vectors are returned.
+    Returns a dict with mu (ascending), X (n x len) if want_vectors, and the
+    bookkeeping needed to map sampled roots onto output positions."""
+    Q = np.asarray(Q, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[0]
+    K = np.asarray(K, dtype=np.float64).reshape(n, -1)
+    k = K.shape[1]
+    s = _sig(sigma, k)
+    U = project(Q, K)
+    defl = deflation_mask(lam, U)
+    keep = np.nonzero(~defl)[0]
+    lam_p = lam[keep]
+    U_p = U[keep]
+    out = dict(U=U, deflated=defl, keep=keep)
+    if sel is not None:
+        r = roots(lam_p, U_p, s, sel=sel, nthreads=nthreads)
+        mu = r["mu"]
+        dl = np.sort(lam[defl])
+        pos = np.asarray(sel, dtype=np.int64) + np.searchsorted(dl, mu, side="left")
+        out.update(mu=mu, pos=pos, roots=r)
+        if want_vectors:
+            Wp = vectors(lam_p, U_p, s, r["origin"], r["tau"])
+            Wfull = np.zeros((n, Wp.shape[1]))
+            Wfull[keep] = Wp
+            out["W"] = Wfull
+            out["X"] = Q @ Wfull
+        return out
+    r = roots(lam_p, U_p, s, nthreads=nthreads) if keep.shape[0] else None
+    mu_s = r["mu"] if r is not None else np.zeros(0)
+    mu_all = np.concatenate([mu_s, lam[defl]])
+    src = np.concatenate([np.arange(mu_s.shape[0]), -1 - np.nonzero(defl)[0]])
+    order = np.argsort(mu_all, kind="stable")
+    out.update(mu=mu_all[order], roots=r, order_src=src[order])
+    if want_vectors:
+        W = np.zeros((n, n))
+        if r is not None:
+            rk = tie_ranks(mu_s, float(np.max(np.abs(lam))) + float(np.sum(U * U)))
+            Wp = vectors(lam_p, U_p, s, r["origin"], r["tau"], rk)
+        for c, sidx in enumerate(src[order]):
+            if sidx >= 0:
+                W[keep, c] = Wp[:, sidx]
+            else:
+                W[-1 - sidx, c] = 1.0
+        out["W"] = W
+        out["X"] = Q @ W
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Result quality (the Sec. 3 accuracy metrics B and C of Figs. 6-7)
+# ---------------------------------------------------------------------------
+def residuals(Q, lam, K, sigma, mu, X):
+    """|A' x_r - mu_r x_r|_2 per column, with A' applied as Q(lam*(Q^T x)) + K Sigma K^T x."""
+    Q = np.asarray(Q, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64).reshape(Q.shape[0], -1)
+    s = _sig(sigma, K.shape[1]).astype(np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    AX = Q @ (np.asarray(lam)[:, None] * (Q.T @ X)) + K @ (s[:, None] * (K.T @ X))
+    return np.linalg.norm(AX - X * np.asarray(mu)[None, :], axis=0)
+
+
+def orthogonality(X):
+    """max |X^T X - I| entry."""
+    X = np.asarray(X, dtype=np.float64)
+    G = X.T @ X
+    return float(np.max(np.abs(G - np.eye(G.shape[0]))))
