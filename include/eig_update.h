@@ -1,0 +1,207 @@
+/*
+ * eig_update.h -- C ABI of the GB300 (sm_103a) rank-k symmetric eigen-update.
+ *
+ * Problem (Oh & Hu, "Multiple-rank Modification of Symmetric Eigenvalue
+ * Problem", arXiv 1706.00773, Sec. 2.1): a symmetric A = Q diag(lambda) Q^T is
+ * known; a symmetric low-rank perturbation K Sigma K^T is added
+ * (Sigma = diag(sigma), sigma_c = +1 or -1; the PSD case K K^T has every
+ * sigma_c = +1).  The library returns the eigenpairs of A' = A + K Sigma K^T:
+ *   U = Q^T K                                   (Sec. 2.1, below eq. (1))
+ *   mu = roots of f(x) = det(I - Sigma U^T (xI - Lambda)^{-1} U)   (eq. (1))
+ *        located by the root count of Sec. 2.2 and refined by the zero finder
+ *        of Sec. 2.3
+ *   X = Q W,  W[:,r] = (Lambda - mu_r I)^{-1} U alpha_r / |.|   (Sec. 2.4, eq. (10))
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major FP64 in device memory.  Q is n x n with
+ *     eigenvectors as columns; K is n x k; U is n x k.
+ *   - lambda is ascending on input and on output (EIG_EINVAL otherwise).
+ *   - sigma is a HOST array of k int8 (+1/-1); NULL means all +1.
+ *   - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Return value 0 = success, negative EIG_E* codes otherwise.  No C++
+ *     exception crosses this boundary.
+ *   - Device arrays passed in are owned by the caller; the library never frees
+ *     them.  The handle owns its workspace (device memory, grown on demand and
+ *     freed by eig_update_destroy).
+ *   - A handle is not thread-safe: one host thread at a time, except
+ *     eig_update_query, which may be called concurrently.
+ */
+#ifndef EIG_UPDATE_H_
+#define EIG_UPDATE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define EIG_OK 0
+#define EIG_EINVAL (-1)   /* bad argument: n<1, k<1, k>EIG_MAX_K, NULL pointer,
+                             unsorted lambda, non-finite input, bad sigma */
+#define EIG_ENOMEM (-2)   /* workspace allocation failed or hbm_budget exceeded */
+#define EIG_ENOTCONV (-3) /* a root hit the iteration cap; results are still
+                             written and the report counts the roots */
+#define EIG_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define EIG_ECUDA (-5)    /* a CUDA runtime call failed */
+#define EIG_ENOTSUP (-6)  /* valid request this build does not implement */
+#define EIG_EBUSY (-7)    /* ticket not finished yet (eig_update_query) */
+
+#define EIG_MAX_K 16      /* largest rank this build accepts */
+
+/* ---- precision modes (eig_init_params.mode) ----------------------------- */
+#define EIG_FP64 0u  /* every step in FP64 on the CUDA cores */
+#define EIG_MIXED 1u /* secular steps in FP64; X = Q W as split-BF16 products
+                        on the tensor cores with exact FP32 chunks and
+                        double-float accumulation */
+
+/* ---- what to compute (eig_problem.want) --------------------------------- */
+#define EIG_VALUES 1u  /* eigenvalues into lambda */
+#define EIG_VECTORS 2u /* eigenvectors into Q (or Q_out) */
+#define EIG_REPORT 4u  /* fill the report's residual / orthogonality checks
+                          (sampled, FP64) */
+#define EIG_ASYNC 8u   /* do not synchronise at the end; the status is then
+                          read with eig_update_query(EIG_Q_LAST_STATUS) */
+
+typedef struct eig_ctx* eig_handle;
+
+typedef struct {
+  int32_t device;      /* CUDA device ordinal */
+  uint32_t mode;       /* EIG_FP64 or EIG_MIXED */
+  uint64_t hbm_budget; /* max bytes of workspace the handle may hold; 0 = no limit */
+  int32_t max_iter;    /* per-root iteration cap of the zero finder; 0 = 128 */
+  uint32_t flags;      /* reserved, must be 0 */
+} eig_init_params;
+
+typedef struct {
+  int64_t n;           /* size, >= 1 */
+  int32_t k;           /* rank, 1..EIG_MAX_K */
+  int32_t pad_;
+  double* Q;           /* device n x n; in: old eigenvectors; out: new ones
+                          unless Q_out is given */
+  double* lambda;      /* device n; in: old eigenvalues ascending; out: new */
+  const double* K;     /* device n x k */
+  const int8_t* sigma; /* host k entries of +1/-1, NULL = all +1 */
+  double* Q_out;       /* device n x n output for the eigenvectors, or NULL */
+  uint32_t want;       /* EIG_VALUES | EIG_VECTORS | EIG_REPORT | EIG_ASYNC */
+  uint32_t pad2_;
+} eig_problem;
+
+typedef struct {
+  int64_t n;            /* problem size */
+  int64_t n_deflated;   /* pairs kept unchanged (|u_i| below the deflation bound) */
+  int64_t iters_total;  /* zero-finder evaluations summed over roots */
+  int64_t n_notconv;    /* roots that hit the iteration cap */
+  int32_t k;
+  int32_t status;       /* final status of this update */
+  int32_t iters_max;    /* largest per-root evaluation count */
+  int32_t n_checked;    /* eigenpairs sampled for the two norms below */
+  double max_residual;  /* max |A' x - mu x|_2 over the sampled pairs */
+  double max_orth;      /* max |x_i^T x_j - delta_ij| over the sampled pairs */
+  double norm_A;        /* max |lambda_old| + |U|_F^2, the scale of A' */
+  double ms_total;      /* device time of the update (CUDA events), ms */
+  /* Device time per stage (CUDA events on the caller's stream), ms: */
+  double ms_project;    /* U = Q^T K */
+  double ms_deflate;    /* deflation and compaction */
+  double ms_counts;     /* root count at every pole */
+  double ms_roots;      /* zero finder, every root */
+  double ms_assemble;   /* eq. (10) columns of W, new eigenvalues */
+  double ms_gemm;       /* X = Q W */
+  int32_t launches;     /* kernels this update launched */
+  int32_t pad_;
+} eig_report;
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/* Create a handle on params->device.  params may be NULL (device 0, FP64,
+   no budget).  On success *out holds the handle.  EIG_EINVAL on bad params,
+   EIG_ECUDA if the device cannot be used. */
+int eig_update_init(const eig_init_params* params, eig_handle* out);
+
+/* Free the handle's workspace and the handle.  NULL is accepted. */
+int eig_update_destroy(eig_handle h);
+
+/* ---- one update ---------------------------------------------------------
+ * Rank-k update of one decomposition (Sec. 2.1-2.4): U = Q^T K, deflation of
+ * rows of U below the bound, root count at every pole, safeguarded Newton /
+ * bisection per root, eq. (10) eigenvector coefficients, X = Q W.  On return
+ * lambda holds the new eigenvalues ascending and Q (or Q_out) the matching
+ * eigenvectors.  Q_out, if given, must not alias Q.  Stream-ordered on
+ * `stream`; unless want has EIG_ASYNC the call synchronises the stream before
+ * returning and returns the final status.  rep (host, may be NULL) receives
+ * the report.  Errors: EIG_EINVAL (arguments, unsorted or non-finite lambda),
+ * EIG_ENOMEM, EIG_ENOTCONV (results written, some roots capped), EIG_ECUDA. */
+int eig_update_rank_k(eig_handle h, eig_problem* prob, eig_report* rep, void* stream);
+
+/* ---- many updates ---------------------------------------------------------
+ * Enqueue `count` independent updates (different n and k allowed) and return
+ * one ticket per problem in tickets[] (host).  Problems whose n is at most
+ * EIG_BATCH_SMALL_N are solved together in one persistent launch (one CTA
+ * per problem); larger ones are solved one after another on the same stream.
+ * Asynchronous: poll with eig_update_query(EIG_Q_STATUS).  The problem
+ * arrays must stay valid until their tickets complete. */
+#define EIG_BATCH_SMALL_N 2048
+int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* tickets,
+                     void* stream);
+
+/* ---- queries --------------------------------------------------------------
+ * what = EIG_Q_STATUS:      in = const uint64_t* ticket, out = int32_t* status
+ *                           (EIG_EBUSY while running; the return value is the
+ *                           same code)
+ * what = EIG_Q_REPORT:      in = const uint64_t* ticket, out = eig_report*
+ * what = EIG_Q_LAST_STATUS: in = NULL, out = int32_t* (synchronises the handle's
+ *                           last stream first)
+ * what = EIG_Q_COUNT:       in = const eig_count_args*, out = NULL.  Root count
+ *                           #{mu < x_j} of diag(lambda) + U Sigma U^T at host or
+ *                           device points (the location sub-problem, Sec. 2.2);
+ *                           synchronous.
+ * what = EIG_Q_WORKSPACE:   in = const eig_problem*, out = uint64_t* bytes the
+ *                           handle needs for that problem.
+ * out_bytes is the size of *out; EIG_EINVAL if too small. */
+#define EIG_Q_STATUS 1
+#define EIG_Q_REPORT 2
+#define EIG_Q_LAST_STATUS 3
+#define EIG_Q_COUNT 4
+#define EIG_Q_WORKSPACE 5
+
+typedef struct {
+  int64_t n;             /* size of the (already projected) problem */
+  int32_t k;
+  int32_t npts;          /* number of evaluation points */
+  const double* lambda;  /* device n, ascending */
+  const double* U;       /* device n x k (column-major) */
+  const int8_t* sigma;   /* host k, NULL = all +1 */
+  const double* x;       /* device npts points */
+  int32_t* counts;       /* device npts output: #{mu < x_j} (at a pole: the
+                            limit from the left) */
+  void* stream;
+} eig_count_args;
+
+int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size_t out_bytes);
+
+/* ---- stage entry points (for callers that hold U already) ----------------- */
+
+/* U = Q^T K (Sec. 2.1).  Q n x n, K n x k, U n x k, all device, column-major.
+   Uses the handle's mode for the arithmetic (FP64 only in this build). */
+int eig_project(eig_handle h, int64_t n, int32_t k, const double* Q, const double* K, double* U,
+                void* stream);
+
+/* Eigenvalues of diag(lambda) + U Sigma U^T (Sec. 2.2-2.3) without vectors:
+   mu (device n, ascending) receives them; iters (device int32 n, may be NULL)
+   the evaluations each root took (0 for deflated pairs).  Synchronous. */
+int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
+                       const int8_t* sigma, double* mu, int32_t* iters, void* stream);
+
+/* Sec. 2.2 Steps 1-2: write K = [(e_j + a)/sqrt(2), (e_j - a)/sqrt(2)] (device
+   n x 2) and sigma = {+1, -1} (host) so that K Sigma K^T = e_j a^T + a e_j^T.
+   a is device n.  Stream-ordered. */
+int eig_make_rank2(int64_t n, int64_t j, const double* a, double* K, int8_t* sigma, void* stream);
+
+/* Library version string (static storage). */
+const char* eig_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIG_UPDATE_H_ */

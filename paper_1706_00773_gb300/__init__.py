@@ -1,0 +1,304 @@
+"""GB300 (sm_103a) rank-k symmetric eigen-update (Oh & Hu, arXiv 1706.00773).
+
+Thin Python binding of the C ABI in ``include/eig_update.h``: the functions
+below carry the same names and only marshal arguments (torch CUDA tensors to
+device pointers, streams, structs).  Every step of the update runs in the CUDA
+kernels of ``libeigupdate.so``; there is no CPU or PyTorch fallback, and
+loading fails with an error when the library has not been built.
+
+Layout: matrices are FP64, column-major (a torch tensor ``Q`` of shape (n, n)
+with strides (1, n), e.g. ``torch.empty(n, n).t()`` or ``colmajor(t)``).
+Q's columns are eigenvectors; lambda is ascending.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "EIG_OK", "EIG_EINVAL", "EIG_ENOMEM", "EIG_ENOTCONV", "EIG_ETIMEOUT", "EIG_ECUDA",
+    "EIG_ENOTSUP", "EIG_EBUSY", "EIG_FP64", "EIG_MIXED", "EIG_VALUES", "EIG_VECTORS",
+    "EIG_REPORT", "EIG_ASYNC", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT", "EIG_Q_LAST_STATUS",
+    "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EigError", "lib", "library_path", "colmajor",
+    "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
+    "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
+    "eig_count", "Updater",
+]
+
+EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
+EIG_ETIMEOUT, EIG_ECUDA, EIG_ENOTSUP, EIG_EBUSY = -4, -5, -6, -7
+EIG_MAX_K = 16
+EIG_FP64, EIG_MIXED = 0, 1
+EIG_VALUES, EIG_VECTORS, EIG_REPORT, EIG_ASYNC = 1, 2, 4, 8
+EIG_Q_STATUS, EIG_Q_REPORT, EIG_Q_LAST_STATUS, EIG_Q_COUNT, EIG_Q_WORKSPACE = 1, 2, 3, 4, 5
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libeigupdate.so")
+
+_NAMES = {EIG_OK: "EIG_OK", EIG_EINVAL: "EIG_EINVAL", EIG_ENOMEM: "EIG_ENOMEM",
+          EIG_ENOTCONV: "EIG_ENOTCONV", EIG_ETIMEOUT: "EIG_ETIMEOUT", EIG_ECUDA: "EIG_ECUDA",
+          EIG_ENOTSUP: "EIG_ENOTSUP", EIG_EBUSY: "EIG_EBUSY"}
+
+
+class EigError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, _NAMES.get(code, "?"), code))
+        self.code = code
+
+
+class eig_init_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("mode", ctypes.c_uint32), ("hbm_budget", ctypes.c_uint64),
+                ("max_iter", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class eig_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("Q", ctypes.c_void_p), ("lambda_", ctypes.c_void_p), ("K", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("Q_out", ctypes.c_void_p), ("want", ctypes.c_uint32),
+                ("pad2_", ctypes.c_uint32)]
+
+
+class eig_report(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_deflated", ctypes.c_int64), ("iters_total", ctypes.c_int64),
+                ("n_notconv", ctypes.c_int64), ("k", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("iters_max", ctypes.c_int32), ("n_checked", ctypes.c_int32),
+                ("max_residual", ctypes.c_double), ("max_orth", ctypes.c_double),
+                ("norm_A", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_project", ctypes.c_double), ("ms_deflate", ctypes.c_double),
+                ("ms_counts", ctypes.c_double), ("ms_roots", ctypes.c_double),
+                ("ms_assemble", ctypes.c_double), ("ms_gemm", ctypes.c_double),
+                ("launches", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class eig_count_args(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("npts", ctypes.c_int32),
+                ("lambda_", ctypes.c_void_p), ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError("libeigupdate.so is not built (run __graft_entry__.build() or "
+                               "python paper_1706_00773_gb300/build.py); the update has no CPU path")
+        L = ctypes.CDLL(library_path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.eig_update_init.argtypes = [ctypes.POINTER(eig_init_params), ctypes.POINTER(vp)]
+        L.eig_update_destroy.argtypes = [vp]
+        L.eig_update_rank_k.argtypes = [vp, ctypes.POINTER(eig_problem), ctypes.POINTER(eig_report), vp]
+        L.eig_update_batch.argtypes = [vp, i32, ctypes.POINTER(eig_problem), ctypes.POINTER(ctypes.c_uint64), vp]
+        L.eig_update_query.argtypes = [vp, i32, vp, vp, ctypes.c_size_t]
+        L.eig_project.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+        L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
+        L.eig_make_rank2.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.eig_version.restype = ctypes.c_char_p
+        for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
+                  "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def colmajor(t):
+    """Column-major (Fortran-order) FP64 copy of a 2-D tensor."""
+    import torch
+
+    t = t.to(torch.float64)
+    return t.t().contiguous().t()
+
+
+def _ptr(t, what: str, cols_major: bool = False):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must be float64" % what)
+    if t.dim() == 2 and cols_major and t.shape[0] > 1 and t.shape[1] > 1 and t.stride() != (1, t.shape[0]):
+        raise ValueError("%s must be column-major (strides (1, rows)); use colmajor()" % what)
+    if t.dim() == 1 and t.stride(0) != 1:
+        raise ValueError("%s must be contiguous" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _sigma_buf(sigma, k):
+    if sigma is None:
+        return None, None
+    vals = [int(v) for v in (sigma.tolist() if hasattr(sigma, "tolist") else sigma)]
+    if len(vals) != k:
+        raise ValueError("sigma must have k entries")
+    buf = (ctypes.c_int8 * k)(*vals)
+    return buf, ctypes.cast(buf, ctypes.c_void_p)
+
+
+def _check(rc: int, what: str, ok=(EIG_OK,)):
+    if rc not in ok:
+        raise EigError(rc, what)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions (same names)
+# ---------------------------------------------------------------------------
+def eig_version() -> str:
+    return lib().eig_version().decode()
+
+
+def eig_update_init(device: int = 0, mode: int = EIG_FP64, hbm_budget: int = 0, max_iter: int = 0):
+    p = eig_init_params(device, mode, hbm_budget, max_iter, 0)
+    h = ctypes.c_void_p()
+    _check(lib().eig_update_init(ctypes.byref(p), ctypes.byref(h)), "eig_update_init")
+    return h
+
+
+def eig_update_destroy(h) -> None:
+    _check(lib().eig_update_destroy(h), "eig_update_destroy")
+
+
+def _problem(Q, lam, K, sigma, want, Q_out=None):
+    n = int(lam.shape[0])
+    k = int(K.shape[1]) if K.dim() == 2 else 1
+    sbuf, sp = _sigma_buf(sigma, k)
+    P = eig_problem(n, k, 0, _ptr(Q, "Q", True), _ptr(lam, "lambda"), _ptr(K, "K", True), sp,
+                    _ptr(Q_out, "Q_out", True) if Q_out is not None else None, want, 0)
+    return P, sbuf
+
+
+def eig_update_rank_k(h, Q, lam, K, sigma=None, want: int = EIG_VALUES | EIG_VECTORS, Q_out=None,
+                      stream=None, raise_on_error: bool = True):
+    """One update in place (lam, and Q unless Q_out).  Returns (status, report dict)."""
+    P, keep = _problem(Q, lam, K, sigma, want, Q_out)
+    rep = eig_report()
+    rc = lib().eig_update_rank_k(h, ctypes.byref(P), ctypes.byref(rep), _stream(stream))
+    del keep
+    if raise_on_error:
+        _check(rc, "eig_update_rank_k", ok=(EIG_OK, EIG_ENOTCONV))
+    return rc, rep.as_dict()
+
+
+def eig_update_batch(h, problems, stream=None):
+    """problems: list of dicts with Q, lam, K[, sigma, want, Q_out].  Returns ticket ids."""
+    arr = (eig_problem * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        P, sb = _problem(p["Q"], p["lam"], p["K"], p.get("sigma"),
+                         p.get("want", EIG_VALUES | EIG_VECTORS), p.get("Q_out"))
+        arr[i] = P
+        keep.append(sb)
+    tickets = (ctypes.c_uint64 * max(1, len(problems)))()
+    _check(lib().eig_update_batch(h, len(problems), arr, tickets, _stream(stream)), "eig_update_batch")
+    _batch_keepalive.append((arr, keep))
+    return [int(tickets[i]) for i in range(len(problems))]
+
+
+_batch_keepalive = []
+
+
+def eig_update_query(h, what: int, ticket: int | None = None):
+    L = lib()
+    if what in (EIG_Q_STATUS, EIG_Q_REPORT):
+        t = ctypes.c_uint64(ticket)
+        if what == EIG_Q_STATUS:
+            out = ctypes.c_int32()
+            rc = L.eig_update_query(h, what, ctypes.byref(t), ctypes.byref(out), ctypes.sizeof(out))
+            return rc
+        rep = eig_report()
+        rc = L.eig_update_query(h, what, ctypes.byref(t), ctypes.byref(rep), ctypes.sizeof(rep))
+        return rc, rep.as_dict()
+    if what == EIG_Q_LAST_STATUS:
+        out = ctypes.c_int32()
+        return L.eig_update_query(h, what, None, ctypes.byref(out), ctypes.sizeof(out))
+    raise ValueError("use eig_count / workspace_bytes for this query")
+
+
+def workspace_bytes(h, n: int, k: int, want: int = EIG_VALUES | EIG_VECTORS, in_place: bool = True) -> int:
+    P = eig_problem(n, k, 0, None, None, None, None, None if in_place else ctypes.c_void_p(1), want, 0)
+    out = ctypes.c_uint64()
+    _check(lib().eig_update_query(h, EIG_Q_WORKSPACE, ctypes.byref(P), ctypes.byref(out),
+                                  ctypes.sizeof(out)), "eig_update_query(WORKSPACE)")
+    return int(out.value)
+
+
+def eig_count(h, lam, U, sigma, x, counts, stream=None) -> None:
+    """#{mu < x_j} for diag(lam) + U Sigma U^T at device points x into int32 counts."""
+    import torch
+
+    n = int(lam.shape[0])
+    k = int(U.shape[1])
+    if counts.dtype != torch.int32 or not counts.is_cuda:
+        raise TypeError("counts must be a CUDA int32 tensor")
+    sbuf, sp = _sigma_buf(sigma, k)
+    a = eig_count_args(n, k, int(x.shape[0]), _ptr(lam, "lambda"), _ptr(U, "U", True), sp,
+                       _ptr(x, "x"), ctypes.c_void_p(counts.data_ptr()), _stream(stream))
+    _check(lib().eig_update_query(h, EIG_Q_COUNT, ctypes.byref(a), None, 0), "eig_update_query(COUNT)")
+    del sbuf
+
+
+def eig_project(h, Q, K, U, stream=None) -> None:
+    n = int(Q.shape[0])
+    k = int(K.shape[1])
+    _check(lib().eig_project(h, n, k, _ptr(Q, "Q", True), _ptr(K, "K", True), _ptr(U, "U", True),
+                             _stream(stream)), "eig_project")
+
+
+def eig_secular_values(h, lam, U, sigma, mu, iters=None, stream=None) -> int:
+    n = int(lam.shape[0])
+    k = int(U.shape[1])
+    sbuf, sp = _sigma_buf(sigma, k)
+    ip = ctypes.c_void_p(iters.data_ptr()) if iters is not None else None
+    rc = lib().eig_secular_values(h, n, k, _ptr(lam, "lambda"), _ptr(U, "U", True), sp, _ptr(mu, "mu"),
+                                  ip, _stream(stream))
+    del sbuf
+    return _check(rc, "eig_secular_values", ok=(EIG_OK, EIG_ENOTCONV))
+
+
+def eig_make_rank2(n: int, j: int, a, K, stream=None):
+    """K (n x 2, column-major) and sigma = (+1, -1) with K Sigma K^T = e_j a^T + a e_j^T."""
+    sig = (ctypes.c_int8 * 2)()
+    _check(lib().eig_make_rank2(n, j, _ptr(a, "a"), _ptr(K, "K", True), ctypes.cast(sig, ctypes.c_void_p),
+                                _stream(stream)), "eig_make_rank2")
+    return [int(sig[0]), int(sig[1])]
+
+
+class Updater:
+    """Handle wrapper: ``Updater(mode).update(Q, lam, K, sigma)``."""
+
+    def __init__(self, device: int = 0, mode: int = EIG_FP64, hbm_budget: int = 0, max_iter: int = 0):
+        self.h = eig_update_init(device, mode, hbm_budget, max_iter)
+
+    def update(self, Q, lam, K, sigma=None, want: int = EIG_VALUES | EIG_VECTORS, Q_out=None, stream=None):
+        return eig_update_rank_k(self.h, Q, lam, K, sigma, want, Q_out, stream)
+
+    def close(self):
+        if self.h:
+            eig_update_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

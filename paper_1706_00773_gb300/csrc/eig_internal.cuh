@@ -1,0 +1,115 @@
+// eig_internal.cuh -- shared declarations of the CUDA path (device helpers and
+// launch wrappers).  Everything here belongs to the product library only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/eig_update.h"
+
+namespace eig {
+
+constexpr int kWarp = 32;
+constexpr double kEps = 2.220446049250313e-16;  // 2^-52, FP64 machine epsilon
+
+// Ranks with a compiled secular kernel; other k are padded with zero columns
+// of U carrying sigma = +1, which leaves the count, det and null vector of the
+// k x k problem unchanged (an extra eigenvalue +1, counted in k_plus).
+__host__ __device__ constexpr int padded_rank(int k) { return k <= 8 ? k : ((k + 1) / 2) * 2; }
+
+// Warps that share one root.  Rows a and K-1-a of the k x k matrices are
+// paired (K+1 upper-triangle entries per pair); pairs are dealt round-robin to
+// the warps so that each warp keeps <= 39 entries of M(x) and of N(x) in
+// registers.
+__host__ __device__ constexpr int warps_per_root(int K) { return K <= 8 ? 1 : K <= 12 ? 2 : 4; }
+
+// Status bits written by the kernels into the handle's device status block.
+enum : int {
+  ST_UNSORTED = 1,
+  ST_NONFINITE = 2,
+  ST_NOTCONV = 4,
+};
+
+// Per-update device status block (one cache line).
+struct DevStatus {
+  int flags;
+  int n_keep;
+  int n_defl;
+  int iters_max;
+  long long iters_total;
+  long long n_notconv;
+  double lam_absmax;
+  double fro2;
+  double lo_sent;
+  double hi_sent;
+};
+
+// The non-deflated sub-problem in the layout the secular kernels read.  Its
+// size n' is only known on the device (written by the deflation kernel), so
+// kernels read it through n_dev and are launched for the worst case ld.
+struct Sub {
+  const int* n_dev; // n' (rows kept), device
+  int ld;           // leading dimension of Us (>= n, multiple of 32)
+  int K;            // padded rank
+  int kplus;        // #{sigma = +1} including padding columns
+  const double* lam;  // n' ascending
+  const double* Us;   // K arrays of ld doubles: Us[c*ld + i] = U'[i][c]
+  const int* idx;     // n': original row index of kept row i
+  const DevStatus* st;       // lo_sent / hi_sent: strict bounds on every root (Weyl)
+  unsigned long long negmask;  // bit c set when sigma_c = -1
+};
+
+// Per-root outputs of the zero finder.
+struct RootOut {
+  int* origin;      // pole index (into Sub) the root is measured from
+  double* tau;      // mu - lam[origin]
+  int* iters;       // evaluations
+  int* flags;       // 1 = hit the cap
+  double* alpha;    // K per root: null vector of Sigma - M(mu) (eq. (10) alpha_0)
+  double* beta;     // 2 per root: u_i^T alpha / (mu - lam_i) at the bracketing poles
+  int* sidx;        // 2 per root: indices of the bracketing poles (-1: none)
+};
+
+// ---- launch wrappers (defined in the .cu files) ----------------------------
+cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* K, double* U,
+                               cudaStream_t s);
+cudaError_t launch_make_rank2(int64_t n, int64_t j, const double* a, double* K, cudaStream_t s);
+cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const double* U,
+                           unsigned long long negmask, double* lam_keep, double* Us, int ld,
+                           int* idx_keep, int* idx_defl, double* lam_defl, DevStatus* st,
+                           cudaStream_t s);
+// Root counts #{mu < x}: at every pole of the sub-problem (x == nullptr,
+// npts = ld, points past n' skipped) or at npts absolute points x.
+cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s);
+cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int* work_counter,
+                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s);
+// mu of every secular root, output positions, new eigenvalues (ascending,
+// merged with the deflated ones) and, when W != nullptr, the eq. (10) columns
+// of W (n x n, column-major, zero-filled beforehand by the caller).
+cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
+                            const double* lam_defl, const DevStatus* st, double* mu_sec,
+                            double* lam_out, double* W, cudaStream_t s);
+cudaError_t launch_gemm_f64(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                            const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+// Same, but skipped on the device when st reports invalid input.
+cudaError_t launch_gemm_f64_guarded(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                                    const double* B, int64_t ldb, double* C, int64_t ldc,
+                                    const DevStatus* st, cudaStream_t s);
+// Small helpers (util.cu).
+cudaError_t launch_copy_guarded(double* dst, const double* src, int64_t count, const DevStatus* st,
+                                cudaStream_t s);
+cudaError_t launch_prepare_undeflated(int64_t n, int k, int K, const double* lam, const double* U,
+                                      double* lam_keep, double* Us, int ld, int* idx_keep,
+                                      DevStatus* st, cudaStream_t s);
+cudaError_t launch_scatter_iters(const Sub& sub, int64_t n, const int* root_iters,
+                                 const double* lam_defl, const double* mu_sec, int* iters_out,
+                                 cudaStream_t s);
+// Residual |A' x - mu x| and pairwise x_i^T x_j for ncols sampled columns
+// (A' = Q diag(lam) Q^T + K Sigma K^T with the OLD Q and lam).  out: ncols
+// residuals followed by ncols*ncols Gram entries.  tmp: 3*n*ncols doubles.
+cudaError_t launch_check_pairs(int64_t n, int k, const double* Q, const double* lam,
+                               const double* K, unsigned long long negmask, const double* X,
+                               const double* mu, const int* cols, int ncols, double* tmp,
+                               double* out, cudaStream_t s);
+
+}  // namespace eig

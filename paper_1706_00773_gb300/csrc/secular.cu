@@ -1,0 +1,810 @@
+// secular.cu -- the FP64 secular stage of the rank-k update.
+//
+//   count(x) = #{mu < x} = #{lam_i < x} + neg(M(x) - Sigma) - k_plus        (1)
+//   M(x) = sum_i u_i u_i^T / (x - lam_i),  N(x) = sum_i u_i u_i^T / (x - lam_i)^2
+//
+// (1) is the integer the modified Sturm chain of Sec. 2.2 (eqs. 4-6) delivers:
+// the number of roots of f(x) = det(I - Sigma U^T (xI - Lambda)^{-1} U) (eq. 1)
+// below x.  It follows from Sylvester's law of inertia applied to the bordered
+// matrix [[Lambda - xI, U], [U^T, -Sigma]], whose two Schur complements are
+// A' - xI and M(x) - Sigma.  It is exact in exact arithmetic, needs no chain
+// construction (the long division of Sec. 2.2 is unstable), and costs one
+// O(n k^2) reduction plus a k x k eigen-decomposition.
+//
+// Kernels
+//   counts_kernel  count at every pole (limit from the left) or at given x:
+//                  the location sub-problem of Sec. 2.1/2.2.
+//   roots_kernel   the root-value sub-problem (Sec. 2.3).  Each root m is first
+//                  placed in the pole interval that holds it (from the pole
+//                  counts), measured from its nearest pole (x = lam_o + tau, so
+//                  that every x - lam_i keeps full relative accuracy), then
+//                  refined by Newton on p(x) = (x - lam_a)(x - lam_b) det(Sigma - M(x))
+//                  (lam_a, lam_b the interval's poles, so p is smooth there),
+//                  safeguarded by bisection on (1) -- the one-point case of the
+//                  paper's divide-and-conquer zero finder.
+//   assemble_*     eq. (10): w_i = (u_i^T alpha_0) / (lam_i - mu), normalised,
+//                  scattered into W; new eigenvalues merged with deflated ones.
+//
+// Work layout.  FP64 runs at 2 DFMA/clk/SM on GB300, so a term (8(k+1) bytes
+// of U and lam) feeds ~k^2 DFMAs: operand traffic is far below L1/L2
+// bandwidth and the kernels read terms straight from global memory (L2
+// resident).  One warp (K <= 8) or a group of 2 or 4 warps (K <= 16) owns a
+// root; lanes split the terms, the warps of a group split the k(k+1)/2 matrix
+// entries (rows a and K-1-a paired, pairs dealt round-robin), and each lane
+// keeps its partial sums in registers.  The k x k eigen-decomposition is a
+// warp-parallel cyclic Jacobi in shared memory.
+#include <math.h>
+
+#include "eig_internal.cuh"
+
+namespace eig {
+namespace {
+
+// ----------------------------------------------------------------------------
+// Compile-time partition of the upper triangle of a K x K matrix.
+// ----------------------------------------------------------------------------
+template <int K, int E>
+__host__ __device__ constexpr int owner_of(int a) {
+  return (a < K - 1 - a ? a : K - 1 - a) % E;
+}
+template <int K, int E, int e>
+__host__ __device__ constexpr int nslots() {
+  int s = 0;
+  for (int a = 0; a < K; ++a)
+    if (owner_of<K, E>(a) == e) s += K - a;
+  return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+template <int E>
+__device__ __forceinline__ void group_sync(int g) {
+  if (E == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(32 * E) : "memory");
+  }
+}
+
+enum { ACC_M = 0, ACC_MN = 1, ACC_MG = 2 };
+
+// Sum over the kept terms of u_i u_i^T * r_i (r_i = 1/(x - lam_i)) into A and,
+// per MODE, of u_i u_i^T r_i^2 into B (ACC_MN) or, for terms sitting exactly on
+// the point (x == lam_i), u_i u_i^T into B (ACC_MG).  x = tau when absolute,
+// else lam_o + tau with x - lam_i formed as tau - (lam_i - lam_o).  Lane 0
+// writes the owned entries of the reduced sums into the symmetric K x K
+// shared-memory matrices sA, sB (row stride K+1).  Returns #{lam_i < x}.
+template <int K, int E, int e, int MODE>
+__device__ __forceinline__ int accumulate(const double* __restrict__ lam,
+                                          const double* __restrict__ Us, int ld, int n,
+                                          double lam_o, bool absolute, double tau, int skip_a,
+                                          int skip_b, double* sA, double* sB, int lane) {
+  constexpr int NS = nslots<K, E, e>();
+  constexpr int KP = K + 1;
+  double A[NS], B[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = 0.0;
+    B[s] = 0.0;
+  }
+  int below = 0;
+  for (int i = lane; i < n; i += 32) {
+    const double li = __ldg(lam + i);
+    const double d = absolute ? (tau - li) : (tau - (li - lam_o));
+    below += (d > 0.0) ? 1 : 0;
+    double u[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) u[c] = __ldg(Us + (size_t)c * ld + i);
+    if (MODE == ACC_MG && d == 0.0) {
+      int s = 0;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        if (owner_of<K, E>(a) == e) {
+#pragma unroll
+          for (int b = a; b < K; ++b) {
+            B[s] = fma(u[a], u[b], B[s]);
+            ++s;
+          }
+        }
+      }
+    } else {
+      // Terms skip_a / skip_b (the poles bracketing a root) are left out of the
+      // sums; the caller carries them exactly in a bordered matrix.
+      const double r = (i == skip_a || i == skip_b) ? 0.0 : 1.0 / d;
+      int s = 0;
+#pragma unroll
+      for (int a = 0; a < K; ++a) {
+        if (owner_of<K, E>(a) == e) {
+          const double ta = u[a] * r;
+          const double tta = ta * r;
+#pragma unroll
+          for (int b = a; b < K; ++b) {
+            A[s] = fma(ta, u[b], A[s]);
+            if (MODE == ACC_MN) B[s] = fma(tta, u[b], B[s]);
+            ++s;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = warp_sum(A[s]);
+    if (MODE != ACC_M) B[s] = warp_sum(B[s]);
+  }
+  below = __reduce_add_sync(0xffffffffu, below);
+  if (lane == 0) {
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (owner_of<K, E>(a) == e) {
+#pragma unroll
+        for (int b = a; b < K; ++b) {
+          sA[a * KP + b] = A[s];
+          sA[b * KP + a] = A[s];
+          if (MODE != ACC_M) {
+            sB[a * KP + b] = B[s];
+            sB[b * KP + a] = B[s];
+          }
+          ++s;
+        }
+      }
+    }
+  }
+  return below;
+}
+
+template <int K, int E, int MODE>
+__device__ __forceinline__ int accumulate_group(int e, const double* __restrict__ lam,
+                                                const double* __restrict__ Us, int ld, int n,
+                                                double lam_o, bool absolute, double tau,
+                                                int skip_a, int skip_b, double* sA, double* sB,
+                                                int lane) {
+  // e is warp-uniform: each warp of a group runs the code for its own rows.
+  if (E == 1 || e == 0)
+    return accumulate<K, E, 0, MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a, skip_b, sA, sB,
+                                     lane);
+  if (E > 1 && e == 1)
+    return accumulate<K, E, (E > 1 ? 1 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
+                                                   skip_b, sA, sB, lane);
+  if (E > 2 && e == 2)
+    return accumulate<K, E, (E > 2 ? 2 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
+                                                   skip_b, sA, sB, lane);
+  return accumulate<K, E, (E > 3 ? 3 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
+                                                 skip_b, sA, sB, lane);
+}
+
+// ----------------------------------------------------------------------------
+// Warp-parallel cyclic Jacobi on a symmetric K x K matrix in shared memory
+// (row stride K+1).  On exit the diagonal of A holds the eigenvalues and, if V
+// is given, V's columns the orthonormal eigenvectors.  Rotation (p,q) is the
+// symmetric 2x2 Schur decomposition; lane r applies it to row/column r.
+// ----------------------------------------------------------------------------
+template <int K>
+__device__ void warp_jacobi(double* A, double* V, int lane) {
+  constexpr int KP = K + 1;
+  if (V) {
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int r = idx / K, c = idx - (idx / K) * K;
+      V[r * KP + c] = (r == c) ? 1.0 : 0.0;
+    }
+  }
+  __syncwarp();
+  if constexpr (K == 1) return;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int r = idx / K, c = idx - (idx / K) * K;
+      const double v = A[r * KP + c];
+      if (r != c) off = fma(v, v, off); else dia = fma(v, v, dia);
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (off == 0.0 || off <= 1e-36 * dia) break;
+    for (int p = 0; p < K - 1; ++p) {
+      for (int q = p + 1; q < K; ++q) {
+        const double apq = A[p * KP + q];
+        const double app = A[p * KP + p];
+        const double aqq = A[q * KP + q];
+        __syncwarp();
+        if (apq == 0.0) continue;
+        if (sweep > 2 && fabs(apq) * 1e18 < fabs(app) && fabs(apq) * 1e18 < fabs(aqq)) {
+          if (lane == 0) {
+            A[p * KP + q] = 0.0;
+            A[q * KP + p] = 0.0;
+          }
+          __syncwarp();
+          continue;
+        }
+        const double theta = (aqq - app) / (2.0 * apq);
+        double t;
+        if (fabs(theta) > 1e150) {
+          t = 0.5 / theta;
+        } else {
+          t = 1.0 / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
+          if (theta < 0.0) t = -t;
+        }
+        const double c = 1.0 / sqrt(fma(t, t, 1.0));
+        const double s = t * c;
+        if (lane < K) {
+          const double arp = A[lane * KP + p], arq = A[lane * KP + q];
+          A[lane * KP + p] = c * arp - s * arq;
+          A[lane * KP + q] = s * arp + c * arq;
+        }
+        __syncwarp();
+        if (lane < K) {
+          const double apr = A[p * KP + lane], aqr = A[q * KP + lane];
+          A[p * KP + lane] = c * apr - s * aqr;
+          A[q * KP + lane] = s * apr + c * aqr;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          A[p * KP + p] = app - t * apq;
+          A[q * KP + q] = aqq + t * apq;
+          A[p * KP + q] = 0.0;
+          A[q * KP + p] = 0.0;
+        }
+        if (V && lane < K) {
+          const double vrp = V[lane * KP + p], vrq = V[lane * KP + q];
+          V[lane * KP + p] = c * vrp - s * vrq;
+          V[lane * KP + q] = s * vrp + c * vrq;
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool input_invalid(const DevStatus* st) {
+  return (st->flags & (ST_UNSORTED | ST_NONFINITE)) != 0;
+}
+
+__device__ __forceinline__ double sigma_of(unsigned long long negmask, int a) {
+  return ((negmask >> a) & 1ull) ? -1.0 : 1.0;
+}
+
+// ----------------------------------------------------------------------------
+// counts_kernel: #{mu < x} at the poles (x == nullptr) or at absolute points.
+// At a point that coincides with poles, the terms on it blow up along
+// R = span{u_i : lam_i = x}; the limit from the left is
+//   #{lam_i < x} + dim R + #{positive eigenvalues of (Sigma - M~(x)) on R^perp} - k_plus
+// with M~ the sum over the other terms.  Away from poles G = 0 and this is (1).
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __restrict__ xs,
+                                                     int npts, int* __restrict__ counts) {
+  constexpr int E = warps_per_root(K);
+  constexpr int G = 4 / E;
+  constexpr int KP = K + 1;
+  __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
+  __shared__ double sEv[G][K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / E, e = warp - (warp / E) * E;
+  if (input_invalid(sub.st)) return;
+  const int n = *sub.n_dev;
+  const bool absolute = (xs != nullptr);
+  const int limit = absolute ? npts : n;
+  // Every group runs the same number of trips so that the named barriers match.
+  for (int base = blockIdx.x * G; base < limit; base += gridDim.x * G) {
+    const int pt = base + g;
+    const bool active = pt < limit;
+    double* M = sM[g];
+    double* Gm = sG[g];
+    int below = 0;
+    if (active) {
+      const double tau = absolute ? xs[pt] : 0.0;
+      const double lam_o = absolute ? 0.0 : sub.lam[pt];
+      below = accumulate_group<K, E, ACC_MG>(e, sub.lam, sub.Us, sub.ld, n, lam_o, absolute, tau,
+                                             -1, -1, M, Gm, lane);
+    }
+    group_sync<E>(g);
+    if (active && e == 0) {
+      for (int idx = lane; idx < K * K; idx += 32) {
+        const int r = idx / K, c = idx - (idx / K) * K;
+        const double v = -M[r * KP + c];
+        M[r * KP + c] = (r == c) ? v + sigma_of(sub.negmask, r) : v;
+      }
+      double gmax = 0.0;
+      for (int idx = lane; idx < K * K; idx += 32) {
+        const int r = idx / K, c = idx - (idx / K) * K;
+        gmax = fmax(gmax, fabs(Gm[r * KP + c]));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, off));
+      __syncwarp();
+      int dimR = 0;
+      if (gmax > 0.0) {
+        double* V = sV[g];
+        warp_jacobi<K>(Gm, V, lane);
+        if (lane < K) sEv[g][lane] = Gm[lane * KP + lane];
+        __syncwarp();
+        double emax = 0.0;
+        for (int j = 0; j < K; ++j) emax = fmax(emax, sEv[g][j]);
+        const double tol = 64.0 * kEps * K * emax;
+        for (int j = 0; j < K; ++j) dimR += (sEv[g][j] > tol) ? 1 : 0;
+        // T = V^T B V into Gm: lane j forms column j.
+        double bv[K];
+        if (lane < K) {
+#pragma unroll
+          for (int r = 0; r < K; ++r) {
+            double acc = 0.0;
+            for (int q = 0; q < K; ++q) acc = fma(M[r * KP + q], V[q * KP + lane], acc);
+            bv[r] = acc;
+          }
+        }
+        __syncwarp();
+        if (lane < K) {
+          for (int i = 0; i < K; ++i) {
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) acc = fma(V[r * KP + i], bv[r], acc);
+            Gm[i * KP + lane] = acc;
+          }
+        }
+        __syncwarp();
+        // Range directions: decouple them with diagonal -1 (never counted).
+        if (lane < K && sEv[g][lane] > tol) {
+          for (int i = 0; i < K; ++i) {
+            Gm[lane * KP + i] = 0.0;
+            Gm[i * KP + lane] = 0.0;
+          }
+        }
+        __syncwarp();
+        if (lane < K && sEv[g][lane] > tol) Gm[lane * KP + lane] = -1.0;
+        __syncwarp();
+        warp_jacobi<K>(Gm, nullptr, lane);
+        M = Gm;
+      } else {
+        warp_jacobi<K>(M, nullptr, lane);
+      }
+      const unsigned pos = __ballot_sync(0xffffffffu, lane < K && M[(lane < K ? lane : 0) * KP + (lane < K ? lane : 0)] > 0.0);
+      const int cnt = below + dimR + __popc(pos) - sub.kplus;
+      if (lane == 0) counts[pt] = cnt;
+      __syncwarp();
+    }
+    group_sync<E>(g);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// roots_kernel: persistent; each root group takes root indices m from a
+// global counter and runs the safeguarded Newton / bisection to convergence.
+//
+// Root m lies in the pole interval (lam_a, lam_b) (a = p-1, b = p; a missing
+// end is a Weyl sentinel).  The two bracketing terms are kept out of the sums
+// and carried exactly in the bordered (K+2) x (K+2) matrix
+//     Z(x) = [[Sigma - M^(x), -u_a, -u_b], [-u_a^T, x - lam_a, 0], [-u_b^T, 0, x - lam_b]]
+// (M^ = M without terms a, b).  Eliminating the last two rows gives back
+// Sigma - M(x), so
+//   det Z = (x - lam_a)(x - lam_b) det(Sigma - M(x)) =: p(x), smooth on the interval,
+//   pos(Sigma - M) = pos(Z) - pos(diag(x - lam_a, x - lam_b))   (inertia), and
+//   Z [c; beta] = 0  <=>  (Sigma - M) c = 0 with beta_i = u_i^T c / (x - lam_i).
+// Z has no entry that blows up near a pole, so the count, the Newton step
+// p'/p = tr(Z^{-1} Z') with Z' = diag(N^, 1, 1), and the null vector keep their
+// accuracy when the root sits next to a pole; eq. (10) then takes
+// w_a = -beta_a, w_b = -beta_b directly instead of u^T c / (lam - mu), which
+// cancels there.  A missing pole is a decoupled entry 1.
+// ----------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restrict__ pole_cnt,
+                                                    int max_iter, int* counter, RootOut out,
+                                                    DevStatus* st) {
+  constexpr int E = warps_per_root(K);
+  constexpr int G = 4 / E;
+  constexpr int KP = K + 1;
+  constexpr int Z2 = K + 2;
+  constexpr int ZP = K + 3;
+  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
+  __shared__ double s_tau[G], s_lamo[G];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / E, e = warp - (warp / E) * E;
+  if (input_invalid(sub.st)) return;
+  const int n = *sub.n_dev;
+  const int ld = sub.ld;
+  const double* __restrict__ lam = sub.lam;
+  const double* __restrict__ Us = sub.Us;
+  for (;;) {
+    if (e == 0 && lane == 0) s_m[g] = atomicAdd(counter, 1);
+    group_sync<E>(g);
+    const int m = s_m[g];
+    if (m >= n) break;
+    // ---- placement (warp 0 of the group; every lane holds the same state) ----
+    int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, slow = 0, ia = -1, ib = -1;
+    bool has_a = false, has_b = false, first = false, notconv = false;
+    double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
+    if (e == 0) {
+      int lo = 0, hi = n;  // p = #{q : pole_cnt[q] <= m}
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pole_cnt[mid] <= m) lo = mid + 1; else hi = mid;
+      }
+      p = lo;
+      has_a = p > 0;
+      has_b = p < n;
+      ia = has_a ? p - 1 : -1;
+      ib = has_b ? p : -1;
+      c_lo = has_a ? pole_cnt[p - 1] : 0;
+      c_hi = has_b ? pole_cnt[p] : n;
+      if (c_lo > m) c_lo = m;
+      if (c_hi <= m) c_hi = m + 1;
+      if (has_a && has_b) {
+        o = p - 1;
+        db = lam[p] - lam[p - 1];
+        tl = 0.0;
+        th = db;
+        tau = 0.5 * db;
+        first = true;
+      } else if (has_a) {
+        o = p - 1;
+        tl = 0.0;
+        th = sub.st->hi_sent - lam[o];
+        tau = 0.5 * th;
+      } else {
+        o = 0;
+        tl = sub.st->lo_sent - lam[0];
+        th = 0.0;
+        tau = 0.5 * tl;
+      }
+      if (lane == 0) {
+        s_tau[g] = tau;
+        s_lamo[g] = lam[o];
+        s_ia[g] = ia;
+        s_ib[g] = ib;
+      }
+    }
+    group_sync<E>(g);
+    const int skip_a = s_ia[g], skip_b = s_ib[g];
+    for (;;) {
+      const double tau_c = s_tau[g];
+      const double lam_o = s_lamo[g];
+      const int below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c,
+                                                       skip_a, skip_b, sM[g], sN[g], lane);
+      group_sync<E>(g);
+      if (e == 0) {
+        const double* M = sM[g];
+        const double* Nm = sN[g];
+        double* Z = sZ[g];
+        double* V = sV[g];
+        const double Da = has_a ? tau - da : 1.0;
+        const double Db = has_b ? tau - db : 1.0;
+        for (int idx = lane; idx < Z2 * Z2; idx += 32) {
+          const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
+          double v;
+          if (r < K && c < K) {
+            v = ((r == c) ? sigma_of(sub.negmask, r) : 0.0) - M[r * KP + c];
+          } else if (r < K || c < K) {
+            const int row = r < K ? r : c;  // component of u
+            const int which = r < K ? c : r;  // K -> pole a, K+1 -> pole b
+            const int pi = (which == K) ? ia : ib;
+            v = (pi >= 0) ? -Us[(size_t)row * ld + pi] : 0.0;
+          } else {
+            v = (r != c) ? 0.0 : (r == K ? Da : Db);
+          }
+          Z[r * ZP + c] = v;
+        }
+        __syncwarp();
+        warp_jacobi<Z2>(Z, V, lane);
+        // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]).
+        double zj = 0.0, contrib = 0.0;
+        if (lane < Z2) {
+          zj = Z[lane * ZP + lane];
+          double q = 0.0;
+          for (int a = 0; a < K; ++a) {
+            double na = 0.0;
+            for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
+            q = fma(V[a * ZP + lane], na, q);
+          }
+          if (has_a) q = fma(V[K * ZP + lane], V[K * ZP + lane], q);
+          if (has_b) q = fma(V[(K + 1) * ZP + lane], V[(K + 1) * ZP + lane], q);
+          contrib = q / zj;
+        }
+        const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
+        const double tsum = warp_sum(contrib);
+        const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
+        const int count = below + __popc(posmask) - posD - sub.kplus;
+        ++it;
+        if (count <= m) {
+          tl = tau;
+          c_lo = count;
+        } else {
+          th = tau;
+          c_hi = count;
+        }
+        if (first) {
+          first = false;
+          if (count <= m) {  // root above the midpoint: measure it from pole b
+            const double sh = -db;
+            tl += sh;
+            th = 0.0;
+            tau += sh;
+            da = sh;
+            db = 0.0;
+            o = p;
+          }
+        }
+        bool conv = false, newton = false;
+        double tn = tau;
+        if (c_hi - c_lo == 1) {
+          const double step = -1.0 / tsum;
+          tn = tau + step;
+          if (step == 0.0) {
+            conv = true;
+            tn = tau;
+          } else if (isfinite(tn) && tn > tl && tn < th) {
+            newton = true;
+            if (fabs(step) <= 2.0 * kEps * fabs(tn)) conv = true;
+            if (fabs(step) > 0.5 * fabs(prev_step)) ++slow; else slow = 0;
+            prev_step = step;
+            if (slow >= 3 && !conv) {
+              newton = false;
+              slow = 0;
+            }
+          }
+        }
+        if (!conv && !newton) {
+          tn = tl + 0.5 * (th - tl);
+          if (tl > 0.0 && th > 64.0 * tl) tn = sqrt(tl) * sqrt(th);
+          else if (th < 0.0 && tl < 64.0 * th) tn = -(sqrt(-tl) * sqrt(-th));
+          if (!(tn > tl && tn < th)) {
+            conv = true;
+            tn = tl + 0.5 * (th - tl);
+          }
+          prev_step = INFINITY;
+        }
+        if (!conv && (th - tl) <= 4.0 * kEps * fmax(fabs(tl), fabs(th))) conv = true;
+        if (!conv && it >= max_iter) {
+          conv = true;
+          notconv = true;
+        }
+        tau = tn;
+        if (conv) {
+          // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
+          int jmin = 0;
+          double amin = fabs(Z[0]);
+          for (int j = 1; j < Z2; ++j) {
+            const double v = fabs(Z[j * ZP + j]);
+            if (v < amin) {
+              amin = v;
+              jmin = j;
+            }
+          }
+          if (lane < K) out.alpha[(size_t)m * K + lane] = V[lane * ZP + jmin];
+          if (lane == 0) {
+            out.beta[2 * (size_t)m] = V[K * ZP + jmin];
+            out.beta[2 * (size_t)m + 1] = V[(K + 1) * ZP + jmin];
+            out.sidx[2 * (size_t)m] = ia;
+            out.sidx[2 * (size_t)m + 1] = ib;
+            out.origin[m] = o;
+            out.tau[m] = tau;
+            out.iters[m] = it;
+            out.flags[m] = notconv ? 1 : 0;
+            atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)it);
+            atomicMax(&st->iters_max, it);
+            if (notconv) {
+              atomicAdd((unsigned long long*)&st->n_notconv, 1ull);
+              atomicOr(&st->flags, (int)ST_NOTCONV);
+            }
+          }
+        }
+        if (lane == 0) {
+          s_tau[g] = tau;
+          s_lamo[g] = lam[o];
+          s_done[g] = conv ? 1 : 0;
+        }
+      }
+      group_sync<E>(g);
+      if (s_done[g]) break;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Assembly: mu of each secular root, output positions, eq. (10) columns.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int lower_bound_d(const double* a, int n, double v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int upper_bound_d(const double* a, int n, double v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void mu_kernel(Sub sub, RootOut roots, double* __restrict__ mu_sec) {
+  if (input_invalid(sub.st)) return;
+  const int n = *sub.n_dev;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+    mu_sec[m] = sub.lam[roots.origin[m]] + roots.tau[m];
+}
+
+// Deflated pairs keep lam_i and the old eigenvector: W column = e_i.
+__global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_defl,
+                                const double* __restrict__ lam_defl, const DevStatus* st,
+                                const double* __restrict__ mu_sec, double* __restrict__ lam_out,
+                                double* __restrict__ W) {
+  if (input_invalid(st)) return;
+  const int nk = *sub.n_dev;
+  const int nd = st->n_defl;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+    const double v = lam_defl[j];
+    const int64_t pos = j + upper_bound_d(mu_sec, nk, v);
+    lam_out[pos] = v;
+    if (W) W[(int64_t)idx_defl[j] + pos * n] = 1.0;
+  }
+}
+
+constexpr int kAsmThreads = 256;
+
+// One CTA per secular root m: w_i = (u_i^T alpha) / (lam_i - mu), |w| = 1, the
+// entry of largest magnitude made positive, scattered to W[idx_i, pos].
+template <int K>
+__global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
+    Sub sub, RootOut roots, int64_t n, const double* __restrict__ lam_defl, const DevStatus* st,
+    const double* __restrict__ mu_sec, double* __restrict__ lam_out, double* __restrict__ W) {
+  __shared__ double s_n2[kAsmThreads];
+  __shared__ double s_mx[kAsmThreads];
+  __shared__ int s_ix[kAsmThreads];
+  if (input_invalid(st)) return;
+  const int nk = *sub.n_dev;
+  const int nd = st->n_defl;
+  const int t = threadIdx.x;
+  for (int m = blockIdx.x; m < nk; m += gridDim.x) {
+    const double mu = mu_sec[m];
+    const int64_t pos = m + lower_bound_d(lam_defl, nd, mu);
+    if (t == 0) lam_out[pos] = mu;
+    if (!W) continue;
+    const int o = roots.origin[m];
+    const double tau = roots.tau[m];
+    const double lam_o = sub.lam[o];
+    const int ia = roots.sidx[2 * (size_t)m], ib = roots.sidx[2 * (size_t)m + 1];
+    const double wa = -roots.beta[2 * (size_t)m], wb = -roots.beta[2 * (size_t)m + 1];
+    double al[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) al[c] = roots.alpha[(size_t)m * K + c];
+    // eq. (10): w_i = u_i^T alpha / (lam_i - mu); the bracketing poles take -beta.
+    auto wcomp = [&](int i) -> double {
+      if (i == ia) return wa;
+      if (i == ib) return wb;
+      double ua = 0.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) ua = fma(sub.Us[(size_t)c * sub.ld + i], al[c], ua);
+      return ua / ((sub.lam[i] - lam_o) - tau);
+    };
+    double n2 = 0.0, mx = -1.0;
+    int ix = 0x7fffffff;
+    for (int i = t; i < nk; i += kAsmThreads) {
+      const double w = wcomp(i);
+      n2 = fma(w, w, n2);
+      if (fabs(w) > mx) {
+        mx = fabs(w);
+        ix = i;
+      }
+    }
+    s_n2[t] = n2;
+    s_mx[t] = mx;
+    s_ix[t] = ix;
+    __syncthreads();
+    for (int s = kAsmThreads / 2; s > 0; s >>= 1) {
+      if (t < s) {
+        s_n2[t] += s_n2[t + s];
+        const double om = s_mx[t + s];
+        const int oi = s_ix[t + s];
+        if (om > s_mx[t] || (om == s_mx[t] && oi < s_ix[t])) {
+          s_mx[t] = om;
+          s_ix[t] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const double nrm = sqrt(s_n2[0]);
+    const int imax = (s_ix[0] >= 0 && s_ix[0] < nk) ? s_ix[0] : 0;  // all-NaN column: any row
+    __syncthreads();
+    const double wmax = wcomp(imax);
+    const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
+    double* col = W + pos * n;
+    for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+  }
+}
+
+int g_occ_roots[17];
+
+template <int K>
+cudaError_t launch_counts_k(const Sub& sub, const double* x, int npts, int* counts,
+                            cudaStream_t s) {
+  constexpr int G = 4 / warps_per_root(K);
+  const int pts = x ? npts : sub.ld;
+  int blocks = (pts + G - 1) / G;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 65535) blocks = 65535;
+  counts_kernel<K><<<blocks, 128, 0, s>>>(sub, x, npts, counts);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_roots_k(const Sub& sub, const int* pole_cnt, int max_iter, int* counter,
+                           const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s) {
+  constexpr int G = 4 / warps_per_root(K);
+  if (g_occ_roots[K] == 0) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, roots_kernel<K>, 128, 0);
+    if (e != cudaSuccess) return e;
+    g_occ_roots[K] = occ > 0 ? occ : 1;
+  }
+  long long want = ((long long)sub.ld + G - 1) / G;
+  long long cap = (long long)num_sms * g_occ_roots[K];
+  int blocks = (int)(want < cap ? want : cap);
+  if (blocks < 1) blocks = 1;
+  roots_kernel<K><<<blocks, 128, 0, s>>>(sub, pole_cnt, max_iter, counter, out, st);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_assemble_k(const Sub& sub, const RootOut& roots, int64_t n,
+                              const int* idx_defl, const double* lam_defl, const DevStatus* st,
+                              double* mu_sec, double* lam_out, double* W, cudaStream_t s) {
+  const int ld = sub.ld;
+  mu_kernel<<<(ld + 255) / 256, 256, 0, s>>>(sub, roots, mu_sec);
+  int blocks = ld < 65535 ? ld : 65535;
+  assemble_kernel<K><<<blocks, kAsmThreads, 0, s>>>(sub, roots, n, lam_defl, st, mu_sec, lam_out, W);
+  int nb = (int)((n + 255) / 256);
+  if (nb > 4096) nb = 4096;
+  deflated_kernel<<<nb, 256, 0, s>>>(sub, n, idx_defl, lam_defl, st, mu_sec, lam_out, W);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s) {
+  switch (sub.K) {
+    case 1: return launch_counts_k<1>(sub, x, npts, counts, s);
+    case 2: return launch_counts_k<2>(sub, x, npts, counts, s);
+    case 3: return launch_counts_k<3>(sub, x, npts, counts, s);
+    case 4: return launch_counts_k<4>(sub, x, npts, counts, s);
+    case 5: return launch_counts_k<5>(sub, x, npts, counts, s);
+    case 6: return launch_counts_k<6>(sub, x, npts, counts, s);
+    case 7: return launch_counts_k<7>(sub, x, npts, counts, s);
+    case 8: return launch_counts_k<8>(sub, x, npts, counts, s);
+    case 10: return launch_counts_k<10>(sub, x, npts, counts, s);
+    case 12: return launch_counts_k<12>(sub, x, npts, counts, s);
+    case 14: return launch_counts_k<14>(sub, x, npts, counts, s);
+    case 16: return launch_counts_k<16>(sub, x, npts, counts, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int* counter,
+                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s) {
+  switch (sub.K) {
+#define R_(K_) case K_: return launch_roots_k<K_>(sub, pole_cnt, max_iter, counter, out, st, num_sms, s);
+    R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8) R_(10) R_(12) R_(14) R_(16)
+#undef R_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
+                            const double* lam_defl, const DevStatus* st, double* mu_sec,
+                            double* lam_out, double* W, cudaStream_t s) {
+  switch (sub.K) {
+#define A_(K_) case K_: return launch_assemble_k<K_>(sub, roots, n, idx_defl, lam_defl, st, mu_sec, lam_out, W, s);
+    A_(1) A_(2) A_(3) A_(4) A_(5) A_(6) A_(7) A_(8) A_(10) A_(12) A_(14) A_(16)
+#undef A_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace eig

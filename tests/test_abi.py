@@ -1,0 +1,70 @@
+"""The C-ABI library loads on the CPU host and exports every symbol the header declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "eig_update.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(eig_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1706_00773_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("eig_update_init", "eig_update_rank_k", "eig_update_batch", "eig_update_query",
+                 "eig_update_destroy", "eig_make_rank2"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    L = ctypes.CDLL(built_lib)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_binding_names_match_header(built_lib):
+    import paper_1706_00773_gb300 as eu
+
+    for name in _declared():
+        assert callable(getattr(eu, name)), name
+    assert eu.eig_version().startswith("eigupdate-gb300")
+
+
+def test_constants_match_header():
+    import paper_1706_00773_gb300 as eu
+
+    txt = open(HEADER).read()
+    for name in ("EIG_OK", "EIG_EINVAL", "EIG_ENOMEM", "EIG_ENOTCONV", "EIG_ETIMEOUT", "EIG_ECUDA",
+                 "EIG_ENOTSUP", "EIG_EBUSY", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT",
+                 "EIG_Q_LAST_STATUS", "EIG_Q_COUNT", "EIG_Q_WORKSPACE"):
+        m = re.search(r"#define %s \(?(-?\d+)\)?" % name, txt)
+        assert m, name
+        assert getattr(eu, name) == int(m.group(1)), name
+    for name in ("EIG_FP64", "EIG_MIXED", "EIG_VALUES", "EIG_VECTORS", "EIG_REPORT", "EIG_ASYNC"):
+        m = re.search(r"#define %s (\d+)u" % name, txt)
+        assert m and getattr(eu, name) == int(m.group(1)), name
+
+
+def test_init_without_gpu_fails_cleanly(built_lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("has a GPU")
+    import paper_1706_00773_gb300 as eu
+
+    with pytest.raises(eu.EigError) as ei:
+        eu.eig_update_init(0)
+    assert ei.value.code == eu.EIG_ECUDA

@@ -1,0 +1,263 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: |mu - mu_oracle| <= 1e-10 ||A||_2; |A'x - mu x| <= 1e-9 ||A||_2;
+root counts bit-exact at points away from the eigenvalues.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_util import cos_match, dev_colmajor, dev_vec, host, norm2_A
+
+pytestmark = pytest.mark.gpu
+
+MU_TOL = 1e-10
+RES_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def eu():
+    import paper_1706_00773_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def handle(eu):
+    h = eu.eig_update_init(0, eu.EIG_FP64)
+    yield h
+    eu.eig_update_destroy(h)
+
+
+def _run_update(eu, h, P, want=None, sigma=None):
+    import torch
+
+    Q = dev_colmajor(P["Q"])
+    lam = dev_vec(P["lam"])
+    K = dev_colmajor(P["K"])
+    s = P["sigma"] if sigma is None else sigma
+    want = want if want is not None else (eu.EIG_VALUES | eu.EIG_VECTORS | eu.EIG_REPORT)
+    rc, rep = eu.eig_update_rank_k(h, Q, lam, K, s, want)
+    torch.cuda.synchronize()
+    return rc, rep, host(lam), host(Q)
+
+
+def _check_full(P, mu, X, tol_mu=MU_TOL, tol_res=RES_TOL, ref=None):
+    ref = ref or oracle.update(P["Q"], P["lam"], P["K"], P["sigma"])
+    scale = norm2_A(P["lam"], P["K"])
+    assert np.all(np.diff(mu) >= 0)
+    err = np.max(np.abs(mu - ref["mu"]))
+    assert err <= tol_mu * scale, err
+    res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu, X)
+    assert np.max(res) <= tol_res * scale, np.max(res)
+    # eigenvectors agree with the oracle's up to sign where the eigenvalue is isolated
+    gaps = np.minimum(np.diff(ref["mu"], prepend=-np.inf), np.diff(ref["mu"], append=np.inf))
+    iso = gaps > 1e-6 * scale
+    if np.any(iso):
+        assert np.min(cos_match(X[:, iso], ref["X"][:, iso])) >= 1 - 1e-9
+    return ref
+
+
+# ---------------------------------------------------------------------------
+def test_project_matches_oracle(eu, handle):
+    import torch
+
+    for n, k in [(1, 1), (37, 3), (300, 8), (513, 16)]:
+        P = workloads.general(n, k, seed=n + k)
+        U = torch.empty((k, n), dtype=torch.float64, device="cuda:0").t()
+        eu.eig_project(handle, dev_colmajor(P["Q"]), dev_colmajor(P["K"]), U)
+        torch.cuda.synchronize()
+        ref = oracle.project(P["Q"], P["K"])
+        assert np.max(np.abs(host(U) - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref))) * np.sqrt(n)
+
+
+def test_make_rank2_matches_oracle(eu):
+    import torch
+
+    n, j = 1000, 123
+    a = np.random.default_rng(0).standard_normal(n)
+    K = torch.empty((2, n), dtype=torch.float64, device="cuda:0").t()
+    sig = eu.eig_make_rank2(n, j, dev_vec(a), K)
+    torch.cuda.synchronize()
+    Kr, sr = oracle.rank2_perturbation(n, j, a)
+    assert sig == [1, -1] and list(sr) == [1, -1]
+    assert np.max(np.abs(host(K) - Kr)) <= 2 * np.finfo(float).eps * np.max(np.abs(Kr))
+
+
+@pytest.mark.parametrize("k,sigma", [(1, "psd"), (1, "nsd"), (2, "mixed"), (3, "mixed"), (4, "psd"),
+                                     (5, "nsd"), (8, "mixed"), (9, "psd"), (12, "mixed"), (16, "mixed")])
+def test_counts_bit_exact(eu, handle, k, sigma):
+    import torch
+
+    n = 150
+    P = workloads.general(n, k, seed=100 + k, sigma=sigma, kscale=0.4)
+    U = oracle.project(P["Q"], P["K"])
+    ev = np.linalg.eigvalsh(oracle.updated_matrix(P["Q"], P["lam"], P["K"], P["sigma"]))
+    scale = norm2_A(P["lam"], P["K"])
+    mids = 0.5 * (ev[1:] + ev[:-1])
+    gaps = np.diff(ev)
+    pts = list(mids[gaps > 1e-6 * scale]) + [ev[0] - 1.0, ev[-1] + 1.0]
+    pts += list(P["lam"][::7])  # exactly at poles (limit from the left)
+    pts = np.array(pts)
+    expect = []
+    for x in pts:
+        if np.any(P["lam"] == x):
+            expect.append(oracle.pole_count(P["lam"], U, P["sigma"], int(np.nonzero(P["lam"] == x)[0][0])))
+        else:
+            expect.append(oracle.count(P["lam"], U, P["sigma"], x))
+    expect = np.array(expect)
+    # where the dense spectrum is unambiguous, the oracle's count is that index
+    far = np.min(np.abs(pts[:, None] - ev[None, :]), axis=1) > 1e-9 * scale
+    assert np.array_equal(expect[far], np.sum(ev[None, :] < pts[far, None], axis=1))
+    counts = torch.zeros(pts.shape[0], dtype=torch.int32, device="cuda:0")
+    eu.eig_count(handle, dev_vec(P["lam"]), dev_colmajor(U), P["sigma"], dev_vec(pts), counts)
+    got = host(counts)
+    assert np.array_equal(got, expect), (got - expect)
+
+
+@pytest.mark.parametrize("n,k,sigma,kind", [(64, 1, "psd", "uniform"), (200, 2, "mixed", "uniform"),
+                                            (333, 4, "nsd", "logspec"), (257, 7, "mixed", "clustered"),
+                                            (300, 8, "psd", "logspec"), (129, 11, "mixed", "uniform"),
+                                            (96, 16, "psd", "uniform")])
+def test_secular_values(eu, handle, n, k, sigma, kind):
+    import torch
+
+    P = workloads.general(n, k, seed=7 * n + k, sigma=sigma, lam_kind=kind)
+    U = oracle.project(P["Q"], P["K"])
+    mu = torch.empty(n, dtype=torch.float64, device="cuda:0")
+    iters = torch.zeros(n, dtype=torch.int32, device="cuda:0")
+    rc = eu.eig_secular_values(handle, dev_vec(P["lam"]), dev_colmajor(U), P["sigma"], mu, iters)
+    assert rc == 0
+    ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], want_vectors=False)
+    assert np.max(np.abs(host(mu) - ref["mu"])) <= MU_TOL * norm2_A(P["lam"], P["K"])
+    assert int(host(iters).max()) < 128
+
+
+def test_rank2_basic_workload(eu, handle):
+    P = workloads.rank2_basic(seed=0, n=256, k=2)
+    rc, rep, mu, X = _run_update(eu, handle, P)
+    assert rc == 0 and rep["status"] == 0
+    _check_full(P, mu, X)
+    assert rep["max_residual"] <= RES_TOL * norm2_A(P["lam"], P["K"])
+    assert rep["max_orth"] <= 1e-12
+
+
+@pytest.mark.parametrize("n,k,sigma", [(1, 1, "psd"), (2, 1, "nsd"), (3, 5, "mixed"), (31, 3, "psd"),
+                                       (33, 2, "mixed"), (100, 9, "nsd"), (257, 13, "mixed"),
+                                       (130, 15, "psd"), (64, 16, "mixed")])
+def test_update_ragged_and_padded(eu, handle, n, k, sigma):
+    P = workloads.general(n, k, seed=n * 31 + k, sigma=sigma, kscale=0.5)
+    rc, rep, mu, X = _run_update(eu, handle, P)
+    assert rc == 0
+    _check_full(P, mu, X)
+
+
+def test_indefinite_rank2_full_size(eu, handle):
+    """One-row-one-column update at n=4096 with 1e-8 clusters and planted deflation."""
+    import torch
+
+    P = workloads.indefinite_rank2(seed=1000, n=4096)
+    n = 4096
+    Q = dev_colmajor(P["Q"])
+    lam = dev_vec(P["lam"])
+    a = dev_vec(P["a"])
+    K = torch.empty((2, n), dtype=torch.float64, device="cuda:0").t()
+    sig = eu.eig_make_rank2(n, P["j"], a, K)
+    rc, rep = eu.eig_update_rank_k(handle, Q, lam, K, sig, eu.EIG_VALUES | eu.EIG_VECTORS | eu.EIG_REPORT)
+    torch.cuda.synchronize()
+    assert rc == 0
+    Kh, sh = oracle.rank2_perturbation(n, P["j"], P["a"])
+    PP = dict(Q=P["Q"], lam=P["lam"], K=Kh, sigma=sh)
+    assert rep["n_deflated"] == len(P["planted"])
+    _check_full(PP, host(lam), host(Q))
+    assert oracle.orthogonality(host(Q)) <= 1e-9
+
+
+def test_general_rank_k_full_size_sampled(eu, handle):
+    """n=8192, k=8: sampled roots and vectors against the oracle, computed one by one."""
+    import torch
+
+    P = workloads.general_rank_k(k=8, seed=2000, n=8192, device="cuda:0")
+    rc, rep, mu, X = _run_update(eu, handle, P)
+    assert rc == 0
+    n = 8192
+    sel = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1],
+                                    np.random.default_rng(5).choice(n, 59, replace=False)]))
+    ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], sel=sel)
+    scale = norm2_A(P["lam"], P["K"])
+    pos = ref["pos"]
+    assert np.max(np.abs(mu[pos] - ref["mu"])) <= MU_TOL * scale
+    assert np.min(cos_match(X[:, pos], ref["X"])) >= 1 - 1e-9
+    res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu[pos], X[:, pos])
+    assert np.max(res) <= RES_TOL * scale
+    assert rep["max_residual"] <= RES_TOL * scale
+
+
+def test_everything_deflates(eu, handle):
+    P = workloads.general(50, 3, seed=1)
+    P["K"] = np.zeros_like(P["K"])
+    rc, rep, mu, X = _run_update(eu, handle, P)
+    assert rc == 0 and rep["n_deflated"] == 50
+    assert np.array_equal(mu, P["lam"])
+    assert np.array_equal(X, P["Q"])
+
+
+def test_invalid_inputs_are_rejected(eu, handle):
+    import torch
+
+    P = workloads.general(40, 2, seed=3)
+    lam_bad = P["lam"].copy()[::-1].copy()
+    Q = dev_colmajor(P["Q"])
+    Qcopy = Q.clone()
+    lam = dev_vec(lam_bad)
+    rc, _ = eu.eig_update_rank_k(handle, Q, lam, dev_colmajor(P["K"]), None,
+                                 eu.EIG_VALUES | eu.EIG_VECTORS, raise_on_error=False)
+    assert rc == eu.EIG_EINVAL
+    assert torch.equal(Q, Qcopy) and np.array_equal(host(lam), lam_bad)
+    lam_nan = P["lam"].copy()
+    lam_nan[5] = np.nan
+    rc, _ = eu.eig_update_rank_k(handle, dev_colmajor(P["Q"]), dev_vec(lam_nan), dev_colmajor(P["K"]),
+                                 None, eu.EIG_VALUES, raise_on_error=False)
+    assert rc == eu.EIG_EINVAL
+    with pytest.raises(eu.EigError):
+        eu.eig_update_rank_k(handle, dev_colmajor(P["Q"]), dev_vec(P["lam"]), dev_colmajor(P["K"]), [1, 2])
+    K17 = dev_colmajor(np.zeros((40, 17)))
+    with pytest.raises(eu.EigError):
+        eu.eig_update_rank_k(handle, dev_colmajor(P["Q"]), dev_vec(P["lam"]), K17)
+
+
+def test_q_out_keeps_input(eu, handle):
+    import torch
+
+    P = workloads.general(120, 4, seed=9, sigma="mixed")
+    Q = dev_colmajor(P["Q"])
+    Qo = torch.empty((120, 120), dtype=torch.float64, device="cuda:0").t()
+    lam = dev_vec(P["lam"])
+    rc, rep = eu.eig_update_rank_k(handle, Q, lam, dev_colmajor(P["K"]), P["sigma"],
+                                   eu.EIG_VALUES | eu.EIG_VECTORS, Q_out=Qo)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert np.array_equal(host(Q), P["Q"])
+    _check_full(P, host(lam), host(Qo))
+
+
+def test_batch_matches_solo(eu, handle):
+    import torch
+
+    probs, devs = [], []
+    for t, (n, k) in enumerate([(64, 1), (200, 3), (129, 8), (300, 5)]):
+        P = workloads.general(n, k, seed=500 + t, sigma="mixed" if k > 1 else "psd")
+        d = dict(Q=dev_colmajor(P["Q"]), lam=dev_vec(P["lam"]), K=dev_colmajor(P["K"]), sigma=P["sigma"],
+                 want=eu.EIG_VALUES | eu.EIG_VECTORS)
+        probs.append(P)
+        devs.append(d)
+    tickets = eu.eig_update_batch(handle, devs)
+    torch.cuda.synchronize()
+    for P, d, t in zip(probs, devs, tickets):
+        assert eu.eig_update_query(handle, eu.EIG_Q_STATUS, t) == 0
+        rc, rep = eu.eig_update_query(handle, eu.EIG_Q_REPORT, t)
+        assert rc == 0 and rep["n"] == P["lam"].shape[0]
+        solo_rc, _, mu_s, X_s = _run_update(eu, handle, P, want=eu.EIG_VALUES | eu.EIG_VECTORS)
+        assert np.array_equal(host(d["lam"]), mu_s)
+        assert np.array_equal(host(d["Q"]), X_s)
