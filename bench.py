@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--cpu-sample", type=int, default=16, help="roots the CPU oracle solves")
+    ap.add_argument("--cpu-sample", type=int, default=2048,
+                    help="roots the CPU oracle solves for cpu_baseline (the reference arm uses a quarter per step)")
+    ap.add_argument("--host-inputs", action="store_true",
+                    help="build the Haar Q with numpy on the host instead of a GPU QR")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return ap.parse_args()
@@ -180,17 +183,18 @@ def run_reference(args):
     import workloads
 
     dev = None
-    try:
-        import torch
+    if not args.host_inputs:
+        try:
+            import torch
 
-        if torch.cuda.is_available():
-            dev = "cuda:0"
-    except Exception:
-        pass
+            if torch.cuda.is_available():
+                dev = "cuda:0"
+        except Exception:
+            pass
     P = workloads.general_rank_k(k=args.k, seed=2000, n=args.n, device=dev)
     n = args.n
     threads = oracle.default_threads()
-    sample = max(1, args.cpu_sample // 2)
+    sample = max(1, args.cpu_sample // 4)
     rng = np.random.default_rng(3)
     for _ in range(args.warmup):
         oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], sel=np.sort(rng.choice(n, 2, replace=False)),
@@ -231,7 +235,7 @@ def main():
     torch.cuda.set_device(dev)
     mode = eu.EIG_MIXED if args.mode == "mixed" else eu.EIG_FP64
     n, k = args.n, args.k
-    P = workloads.general_rank_k(k=k, seed=2000 + rank, n=n, device=dev)
+    P = workloads.general_rank_k(k=k, seed=2000 + rank, n=n, device=None if args.host_inputs else dev)
     Q = torch.from_numpy(np.asfortranarray(P["Q"])).to(dev)
     lam0 = torch.from_numpy(P["lam"]).to(dev)
     K = torch.from_numpy(np.asfortranarray(P["K"])).to(dev)
