@@ -47,6 +47,8 @@ extern "C" {
 #define EIG_ECUDA (-5)    /* a CUDA runtime call failed */
 #define EIG_ENOTSUP (-6)  /* valid request this build does not implement */
 #define EIG_EBUSY (-7)    /* ticket not finished yet (eig_update_query) */
+#define EIG_ETOOBIG (-8)  /* problem larger than eig_secular_values_static's
+                             fixed scratch holds (n > EIG_STATIC_MAX_N) */
 
 #define EIG_MAX_K 16      /* largest rank this build accepts */
 
@@ -192,6 +194,28 @@ int eig_project(eig_handle h, int64_t n, int32_t k, const double* Q, const doubl
    the evaluations each root took (0 for deflated pairs).  Synchronous. */
 int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
                        const int8_t* sigma, double* mu, int32_t* iters, void* stream);
+
+/* ---- eigenvalues without any device allocation ---------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: code whose HBM is owned by another memory
+ * manager (a framework's caching allocator, a serving process that reserves
+ * memory up front) and latency-critical loops that cannot absorb a
+ * cudaMalloc/cudaFree (cudaFree synchronises the device).  It computes what
+ * eig_secular_values computes, for n <= EIG_STATIC_MAX_N and k <= EIG_MAX_K,
+ * with every temporary in one fixed 3 MiB device array that the library
+ * defines at file scope; the caller passes inputs and outputs only, and no
+ * handle is needed.  Larger problems return EIG_ETOOBIG.
+ *   - Every GPU that loads the library holds that array until the process exits.
+ *   - All calls share the array: calls whose work overlaps on the GPU (two
+ *     streams or two host threads at once) race and give wrong results.
+ *   - The first call on a device looks up the array's device address (set-up,
+ *     with that device current); make that first call before any stream capture.
+ * Arguments as eig_secular_values (device lambda, U, mu, iters; host sigma),
+ * plus max_iter (0 = 128).  Synchronises `stream` before returning. */
+#define EIG_STATIC_MAX_N 8192
+int eig_secular_values_static(int64_t n, int32_t k, const double* lambda, const double* U,
+                              const int8_t* sigma, double* mu, int32_t* iters, int32_t max_iter,
+                              void* stream);
 
 /* Sec. 2.2 Steps 1-2: write K = [(e_j + a)/sqrt(2), (e_j - a)/sqrt(2)] (device
    n x 2) and sigma = {+1, -1} (host) so that K Sigma K^T = e_j a^T + a e_j^T.

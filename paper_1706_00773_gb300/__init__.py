@@ -22,11 +22,12 @@ __all__ = [
     "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EigError", "lib", "library_path", "colmajor",
     "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
     "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
-    "eig_count", "Updater",
+    "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
-EIG_ETIMEOUT, EIG_ECUDA, EIG_ENOTSUP, EIG_EBUSY = -4, -5, -6, -7
+EIG_ETIMEOUT, EIG_ECUDA, EIG_ENOTSUP, EIG_EBUSY, EIG_ETOOBIG = -4, -5, -6, -7, -8
+EIG_STATIC_MAX_N = 8192
 EIG_MAX_K = 16
 EIG_FP64, EIG_MIXED = 0, 1
 EIG_VALUES, EIG_VECTORS, EIG_REPORT, EIG_ASYNC = 1, 2, 4, 8
@@ -37,7 +38,7 @@ library_path = os.path.join(_HERE, "libeigupdate.so")
 
 _NAMES = {EIG_OK: "EIG_OK", EIG_EINVAL: "EIG_EINVAL", EIG_ENOMEM: "EIG_ENOMEM",
           EIG_ENOTCONV: "EIG_ENOTCONV", EIG_ETIMEOUT: "EIG_ETIMEOUT", EIG_ECUDA: "EIG_ECUDA",
-          EIG_ENOTSUP: "EIG_ENOTSUP", EIG_EBUSY: "EIG_EBUSY"}
+          EIG_ENOTSUP: "EIG_ENOTSUP", EIG_EBUSY: "EIG_EBUSY", EIG_ETOOBIG: "EIG_ETOOBIG"}
 
 
 class EigError(RuntimeError):
@@ -99,9 +100,11 @@ def lib() -> ctypes.CDLL:
         L.eig_project.argtypes = [vp, i64, i32, vp, vp, vp, vp]
         L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
         L.eig_make_rank2.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.eig_secular_values_static.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp]
         L.eig_version.restype = ctypes.c_char_p
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
-                  "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2"):
+                  "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
+                  "eig_secular_values_static"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -273,6 +276,19 @@ def eig_secular_values(h, lam, U, sigma, mu, iters=None, stream=None) -> int:
                                   ip, _stream(stream))
     del sbuf
     return _check(rc, "eig_secular_values", ok=(EIG_OK, EIG_ENOTCONV))
+
+
+def eig_secular_values_static(lam, U, sigma, mu, iters=None, max_iter: int = 0, stream=None) -> int:
+    """eig_secular_values without any device allocation (fixed library scratch,
+    n <= EIG_STATIC_MAX_N); returns the status code without raising."""
+    n = int(lam.shape[0])
+    k = int(U.shape[1])
+    sbuf, sp = _sigma_buf(sigma, k)
+    ip = ctypes.c_void_p(iters.data_ptr()) if iters is not None else None
+    rc = lib().eig_secular_values_static(n, k, _ptr(lam, "lambda"), _ptr(U, "U", True), sp, _ptr(mu, "mu"),
+                                         ip, max_iter, _stream(stream))
+    del sbuf
+    return rc
 
 
 def eig_make_rank2(n: int, j: int, a, K, stream=None):

@@ -64,6 +64,7 @@ __device__ __forceinline__ int ub(const double* a, int n, double v) {
 __global__ void scatter_iters_kernel(Sub sub, int64_t n, const int* __restrict__ root_iters,
                                      const double* __restrict__ lam_defl,
                                      const double* __restrict__ mu_sec, int* __restrict__ out) {
+  if (sub.st->flags & (ST_UNSORTED | ST_NONFINITE)) return;
   const int nk = *sub.n_dev;
   const int nd = sub.st->n_defl;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
