@@ -7,7 +7,10 @@ sigma = +1.  Inputs stay resident in HBM; every step restores lam (64 KB) and
 writes the new eigenvectors to a second buffer, so each step does identical
 work on inputs far larger than L2 (Q and W are 537 MB each).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode mixed|fp64]
+
+The headline is the mixed path (X = Q W on the tensor cores, everything else
+FP64); the plain FP64 path is timed beside it on the same inputs.
     python bench.py --impl reference ...   (the CPU oracle arm)
 
 Prints one JSON line on rank 0.
@@ -42,10 +45,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--cpu-sample", type=int, default=2048,
+    ap.add_argument("--cpu-sample", type=int, default=6144,
                     help="roots the CPU oracle solves for cpu_baseline (the reference arm uses a quarter per step)")
     ap.add_argument("--host-inputs", action="store_true",
                     help="build the Haar Q with numpy on the host instead of a GPU QR")
@@ -219,6 +223,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_mode(eu, h, P, dev, steps, warmup, world):
+    """Time `steps` complete updates on resident inputs; returns timings and reports."""
+    import numpy as np
+    import torch
+
+    n = P["lam"].shape[0]
+    k = P["K"].shape[1]
+    Q = torch.from_numpy(np.asfortranarray(P["Q"])).to(dev)
+    lam0 = torch.from_numpy(P["lam"]).to(dev)
+    K = torch.from_numpy(np.asfortranarray(P["K"])).to(dev)
+    lam = lam0.clone()
+    X = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    want = eu.EIG_VALUES | eu.EIG_VECTORS
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lam.copy_(lam0)
+        rc, rep = eu.eig_update_rank_k(h, Q, lam, K, P["sigma"], want, Q_out=X, stream=stream)
+        assert rc == 0, rc
+        return rep
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = []
+    e0.record(stream)
+    for _ in range(steps):
+        reps.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(world, e0.elapsed_time(e1))
+    lat = sorted(r["ms_total"] for r in reps)
+    del Q, K, X
+    return {"ms": ms, "value": world * n * steps / (ms / 1000.0), "reps": reps,
+            "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -233,75 +287,46 @@ def main():
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    mode = eu.EIG_MIXED if args.mode == "mixed" else eu.EIG_FP64
     n, k = args.n, args.k
     P = workloads.general_rank_k(k=k, seed=2000 + rank, n=n, device=None if args.host_inputs else dev)
-    Q = torch.from_numpy(np.asfortranarray(P["Q"])).to(dev)
-    lam0 = torch.from_numpy(P["lam"]).to(dev)
-    K = torch.from_numpy(np.asfortranarray(P["K"])).to(dev)
-    lam = lam0.clone()
-    X = torch.empty((n, n), dtype=torch.float64, device=dev).t()
-    h = eu.eig_update_init(local, mode)
-    want = eu.EIG_VALUES | eu.EIG_VECTORS
-    stream = torch.cuda.current_stream()
-
-    def step():
-        lam.copy_(lam0)
-        rc, rep = eu.eig_update_rank_k(h, Q, lam, K, P["sigma"], want, Q_out=X, stream=stream)
-        assert rc == 0, rc
-        return rep
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    barrier(world)
+    main_mode = eu.EIG_MIXED if args.mode == "mixed" else eu.EIG_FP64
+    h = eu.eig_update_init(local, main_mode)
     clocks = ClockSampler(local)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = []
-    torch.cuda.synchronize()
-    barrier(world)
-    e0.record(stream)
-    for _ in range(args.steps):
-        reps.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    R = run_mode(eu, h, P, dev, args.steps, args.warmup, world)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(world, ms_total)
-    value = world * n * args.steps / (ms_max / 1000.0)
-    lat = sorted(r["ms_total"] for r in reps)
-    p50 = float(np.percentile(lat, 50))
-    p99 = float(np.percentile(lat, 99))
+    reps = R["reps"]
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
-    # Host buffers hold the transposes row-major, i.e. the matrices column-major,
-    # so every copy is one contiguous transfer.
-    Qh = torch.from_numpy(np.ascontiguousarray(P["Q"].T)).pin_memory()
-    Kh = torch.from_numpy(np.ascontiguousarray(P["K"].T)).pin_memory()
-    lamh = torch.from_numpy(P["lam"].copy()).pin_memory()
-    Xh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    lamo = torch.empty(n, dtype=torch.float64).pin_memory()
-    Qd_rm = torch.empty((n, n), dtype=torch.float64, device=dev)
-    Kd_rm = torch.empty((k, n), dtype=torch.float64, device=dev)
-    Qd, Kd = Qd_rm.t(), Kd_rm.t()
-    lamd = torch.empty(n, dtype=torch.float64, device=dev)
-    X_rm = X.t()
-    e2e_steps = max(1, min(args.steps, 3))
-
-    def e2e_step():
-        Qd_rm.copy_(Qh, non_blocking=True)
-        Kd_rm.copy_(Kh, non_blocking=True)
-        lamd.copy_(lamh, non_blocking=True)
-        rc, _ = eu.eig_update_rank_k(h, Qd, lamd, Kd, P["sigma"], want, Q_out=X, stream=stream)
-        assert rc == 0
-        Xh.copy_(X_rm, non_blocking=True)
-        lamo.copy_(lamd, non_blocking=True)
-
     e2e_value = None
+    h2d = (n * n + n * k + n) * 8
+    d2h = (n * n + n) * 8
+    stream = torch.cuda.current_stream()
     if not args.no_e2e:
+        # Host buffers hold the transposes row-major, i.e. the matrices column-major,
+        # so every copy is one contiguous transfer.
+        Qh = torch.from_numpy(np.ascontiguousarray(P["Q"].T)).pin_memory()
+        Kh = torch.from_numpy(np.ascontiguousarray(P["K"].T)).pin_memory()
+        lamh = torch.from_numpy(P["lam"].copy()).pin_memory()
+        Xh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        lamo = torch.empty(n, dtype=torch.float64).pin_memory()
+        Qd_rm = torch.empty((n, n), dtype=torch.float64, device=dev)
+        Kd_rm = torch.empty((k, n), dtype=torch.float64, device=dev)
+        Xd_rm = torch.empty((n, n), dtype=torch.float64, device=dev)
+        lamd = torch.empty(n, dtype=torch.float64, device=dev)
+        want = eu.EIG_VALUES | eu.EIG_VECTORS
+
+        def e2e_step():
+            Qd_rm.copy_(Qh, non_blocking=True)
+            Kd_rm.copy_(Kh, non_blocking=True)
+            lamd.copy_(lamh, non_blocking=True)
+            rc, _ = eu.eig_update_rank_k(h, Qd_rm.t(), lamd, Kd_rm.t(), P["sigma"], want, Q_out=Xd_rm.t(),
+                                         stream=stream)
+            assert rc == 0
+            Xh.copy_(Xd_rm, non_blocking=True)
+            lamo.copy_(lamd, non_blocking=True)
+
+        e2e_steps = max(1, min(args.steps, 3))
         e2e_step()
         torch.cuda.synchronize()
         barrier(world)
@@ -314,43 +339,62 @@ def main():
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(world, f0.elapsed_time(f1))
         e2e_value = world * n * e2e_steps / (e2e_ms / 1000.0)
-    h2d = (n * n + n * k + n) * 8
-    d2h = (n * n + n) * 8
+        del Qd_rm, Kd_rm, Xd_rm
+    eu.eig_update_destroy(h)
 
-    # ---- roofline of the dominant kernel, from the library's own events
+    # ---- the plain FP64 path on the same inputs (the comparison the metric names)
+    fp64 = None
+    if main_mode == eu.EIG_MIXED and not args.no_fp64_path:
+        h64 = eu.eig_update_init(local, eu.EIG_FP64)
+        R64 = run_mode(eu, h64, P, dev, max(1, min(args.steps, 3)), 3, world)
+        eu.eig_update_destroy(h64)
+        fp64 = {"value": R64["value"], "unit": UNIT, "ms_per_step": R64["ms"] / len(R64["reps"]),
+                "latency_ms": {"p50": R64["p50"], "p99": R64["p99"]}}
+
+    # ---- rooflines from the library's own per-stage CUDA events
+    peaks, psrc = measured_peaks()
     mean = lambda key: statistics.fmean(r[key] for r in reps)
     stage = {key: mean(key) for key in ("ms_project", "ms_deflate", "ms_counts", "ms_roots", "ms_assemble",
-                                        "ms_gemm")}
+                                        "ms_slice", "ms_gemm")}
     n_keep = n - int(reps[-1]["n_deflated"])
     evals = statistics.fmean(r["iters_total"] for r in reps)
-    if stage["ms_roots"] >= stage["ms_gemm"]:
-        kname = "roots_kernel"
-        flops = secular_flops(n_keep, k, evals)
-        dur = stage["ms_roots"]
-        unit_note = "zero finder: %.0f evaluations x n'(2k(k+1)+2) FP64 flops" % evals
+    roots_flops = secular_flops(n_keep, k, evals)
+    roots_ach = roots_flops / (stage["ms_roots"] / 1000.0) / 1e9
+    roof_roots = {"kernel": "roots_kernel", "bound": "alu", "achieved": roots_ach, "peak": FP64_PEAK_GFLOPS,
+                  "unit": "GFLOP/s", "frac": roots_ach / FP64_PEAK_GFLOPS, "traffic": load_traffic("roots_kernel"),
+                  "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
+                  "work": "%.0f evaluations x n'(2k(k+1)+2) FP64 flops per launch" % evals}
+    if main_mode == eu.EIG_MIXED:
+        gflops = 15 * 2.0 * n ** 3
+        peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1000.0
+        g_ach = gflops / (stage["ms_gemm"] / 1000.0) / 1e9
+        roof_gemm = {"kernel": "gemm_tc_kernel", "bound": "tensor", "achieved": g_ach / 1000.0, "peak": peak_t / 1000.0,
+                     "unit": "TFLOP/s", "frac": g_ach / peak_t, "traffic": load_traffic("gemm_tc_kernel"),
+                     "peak_source": "bf16 dense, sustained, %s (MEASURED_PEAKS.json)" % psrc,
+                     "work": "15 BF16 slice-pair products x 2 n^3 (useful FP64-equivalent 2 n^3 = %.3g)" % (2.0 * n ** 3)}
     else:
-        kname = "gemm_f64_kernel" if mode == eu.EIG_FP64 else "gemm_tc_kernel"
-        flops = 2.0 * n * n * n
-        dur = stage["ms_gemm"]
-        unit_note = "X = Q W: 2 n^3 flops"
-    achieved = flops / (dur / 1000.0) / 1e9
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-            "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": load_traffic(kname),
-            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
-            "work": unit_note}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        gflops = 2.0 * n ** 3
+        g_ach = gflops / (stage["ms_gemm"] / 1000.0) / 1e9
+        roof_gemm = {"kernel": "gemm_f64_kernel", "bound": "alu", "achieved": g_ach, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": g_ach / FP64_PEAK_GFLOPS, "traffic": load_traffic("gemm_f64_kernel"),
+                     "peak_source": "FP64 pipe (recipe nominal)", "work": "2 n^3 flops"}
+    dominant = roof_roots if stage["ms_roots"] >= stage["ms_gemm"] else roof_gemm
+    other = roof_gemm if dominant is roof_roots else roof_roots
+    line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": R["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "k": k, "mode": args.mode,
-                       "l2": "inputs larger than L2 (Q, W, X 537 MB each)", "parallelism": "independent update per GPU"},
-            "latency_ms": {"p50": p50, "p99": p99},
+                       "l2": "inputs larger than L2 (Q, X 537 MB; W slices 671 MB)",
+                       "parallelism": "independent update per GPU"},
+            "latency_ms": {"p50": R["p50"], "p99": R["p99"]},
+            "fp64_path": fp64,
+            "speedup_vs_fp64_path": (R["value"] / fp64["value"]) if fp64 else None,
             "stages_ms": stage, "evals_per_root": evals / max(1, n_keep),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
-            "roofline": roof, "clocks": clk}
+            "roofline": dominant, "roofline_other": other, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P, args.cpu_sample)
-    eu.eig_update_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -109,6 +109,7 @@ typedef struct {
   double ms_counts;     /* root count at every pole */
   double ms_roots;      /* zero finder, every root */
   double ms_assemble;   /* eq. (10) columns of W, new eigenvalues */
+  double ms_slice;      /* EIG_MIXED: BF16 digit slices of Q (0 in EIG_FP64) */
   double ms_gemm;       /* X = Q W */
   int32_t launches;     /* kernels this update launched */
   int32_t pad_;

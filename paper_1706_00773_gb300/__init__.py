@@ -67,7 +67,7 @@ class eig_report(ctypes.Structure):
                 ("norm_A", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_project", ctypes.c_double), ("ms_deflate", ctypes.c_double),
                 ("ms_counts", ctypes.c_double), ("ms_roots", ctypes.c_double),
-                ("ms_assemble", ctypes.c_double), ("ms_gemm", ctypes.c_double),
+                ("ms_assemble", ctypes.c_double), ("ms_slice", ctypes.c_double), ("ms_gemm", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def as_dict(self) -> dict:

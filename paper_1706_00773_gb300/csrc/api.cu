@@ -51,6 +51,11 @@ struct Carve {
   double* lam_old = nullptr;
   double* W = nullptr;
   double* X = nullptr;
+  __nv_bfloat16* Qs = nullptr;   // mixed mode: slices of Q
+  __nv_bfloat16* Ws = nullptr;   // mixed mode: slices of W
+  int* erow = nullptr;
+  int* fcol = nullptr;
+  unsigned long long* rmax = nullptr;
   double* chk_tmp = nullptr;
   double* chk_out = nullptr;
   int* chk_cols = nullptr;
@@ -58,7 +63,7 @@ struct Carve {
   size_t bytes = 0;
 };
 
-Carve plan(char* base, int64_t n, int k, bool vectors, bool xbuf, bool report) {
+Carve plan(char* base, int64_t n, int k, bool vectors, bool xbuf, bool report, bool mixed = false) {
   Carve c;
   const int K = padded_rank(k);
   const size_t ld = align_up((size_t)n, 32);
@@ -91,7 +96,16 @@ Carve plan(char* base, int64_t n, int k, bool vectors, bool xbuf, bool report) {
     c.chk_out = reinterpret_cast<double*>(take(sizeof(double) * (kCheckCols + kCheckCols * kCheckCols)));
     c.chk_cols = reinterpret_cast<int*>(take(sizeof(int) * kCheckCols));
   }
-  if (vectors) c.W = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n * n));
+  if (vectors && mixed) {
+    const size_t planes = (size_t)tc_num_slices() * tc_slice_plane((int)n);
+    c.Qs = reinterpret_cast<__nv_bfloat16*>(take(2 * planes));
+    c.Ws = reinterpret_cast<__nv_bfloat16*>(take(2 * planes));
+    c.erow = reinterpret_cast<int*>(take(sizeof(int) * ld));
+    c.fcol = reinterpret_cast<int*>(take(sizeof(int) * ld));
+    c.rmax = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * ld));
+  } else if (vectors) {
+    c.W = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n * n));
+  }
   if (vectors && xbuf) c.X = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n * n));
   c.bytes = off;
   return c;
@@ -112,6 +126,7 @@ struct DeviceGuard {
 
 int status_of(const DevStatus& s) {
   if (s.flags & (ST_UNSORTED | ST_NONFINITE)) return EIG_EINVAL;
+  if (s.flags & ST_TIMEOUT) return EIG_ETIMEOUT;
   if (s.flags & ST_NOTCONV) return EIG_ENOTCONV;
   return EIG_OK;
 }
@@ -128,7 +143,7 @@ struct eig_ctx {
   size_t ws_bytes = 0;
   DevStatus* st_host = nullptr;  // pinned
   double* chk_host = nullptr;    // pinned
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[9] = {};
   cudaStream_t last_stream = nullptr;
   int last_launches = 0;
   bool last_pending = false;
@@ -186,7 +201,7 @@ bool sigma_info(const int8_t* sigma, int k, unsigned long long* negmask, int* kp
   } while (0)
 
 // Stages a2-a9 (+ the optional check) of one update, stream-ordered.  With
-// ev != nullptr, events 0..7 are recorded at the stage boundaries.
+// ev != nullptr, events 0..8 are recorded at the stage boundaries.
 int enqueue_update(eig_ctx* h, const eig_problem* P, const Carve& c, cudaStream_t s,
                    unsigned long long negmask, int kplus_k, cudaEvent_t* ev, int* launches) {
   int nl = 0;
@@ -198,6 +213,7 @@ int enqueue_update(eig_ctx* h, const eig_problem* P, const Carve& c, cudaStream_
   const int ld = (int)align_up((size_t)n, 32);
   const bool vectors = (P->want & EIG_VECTORS) != 0;
   const bool report = (P->want & EIG_REPORT) != 0;
+  const bool mixed = vectors && h->mode == EIG_MIXED;
   MARK(0);
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(launch_project_f64(n, k, P->Q, P->K, c.U, s));
@@ -226,27 +242,42 @@ int enqueue_update(eig_ctx* h, const eig_problem* P, const Carve& c, cudaStream_
   CK(launch_roots(sub, c.pole_cnt, h->max_iter, c.counter, ro, c.st, h->num_sms, s));
   ++nl;
   MARK(4);
-  if (vectors) CK(cudaMemsetAsync(c.W, 0, sizeof(double) * (size_t)n * n, s));
+  WSlices ws;
+  if (mixed) {
+    ws.Ws = c.Ws;
+    ws.plane = tc_slice_plane((int)n);
+    ws.lds = tc_slice_ld((int)n);
+    ws.fcol = c.fcol;
+    CK(cudaMemsetAsync(c.Ws, 0, 2 * (size_t)tc_num_slices() * ws.plane, s));
+  } else if (vectors) {
+    CK(cudaMemsetAsync(c.W, 0, sizeof(double) * (size_t)n * n, s));
+  }
   // lam_old keeps the old eigenvalues, so the new ones go straight into lambda.
   CK(launch_assemble(sub, ro, n, c.idx_defl, c.lam_defl, c.st, c.mu_sec, P->lambda,
-                     vectors ? c.W : nullptr, s));
+                     (vectors && !mixed) ? c.W : nullptr, s, ws));
   nl += 3;
   MARK(5);
   if (vectors) {
     double* Xdst = P->Q_out ? P->Q_out : c.X;
-    CK(launch_gemm_f64_guarded(n, n, n, P->Q, n, c.W, n, Xdst, n, c.st, s));
-    ++nl;
+    if (mixed) {
+      CK(launch_slice_q((int)n, P->Q, c.rmax, c.erow, c.Qs, c.st, s));
+      MARK(6);
+      CK(launch_gemm_tc((int)n, c.Qs, c.Ws, c.erow, c.fcol, Xdst, (int)n, c.st, &c.st->flags, s));
+      nl += 3;
+    } else {
+      MARK(6);
+      CK(launch_gemm_f64_guarded(n, n, n, P->Q, n, c.W, n, Xdst, n, c.st, s));
+      ++nl;
+    }
+    MARK(7);
     if (report) {
       int cols[kCheckCols];
       const int nc = (int)(n < kCheckCols ? n : kCheckCols);
       for (int i = 0; i < nc; ++i) cols[i] = (int)((int64_t)i * (n - 1) / (nc > 1 ? nc - 1 : 1));
       CK(cudaMemcpyAsync(c.chk_cols, cols, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-      MARK(6);
       CK(launch_check_pairs(n, k, P->Q, c.lam_old, P->K, negmask, Xdst, P->lambda, c.chk_cols, nc,
                             c.chk_tmp, c.chk_out, s));
       nl += 6;
-    } else {
-      MARK(6);
     }
     if (!P->Q_out) {
       CK(launch_copy_guarded(P->Q, c.X, n * n, c.st, s));
@@ -254,8 +285,9 @@ int enqueue_update(eig_ctx* h, const eig_problem* P, const Carve& c, cudaStream_
     }
   } else {
     MARK(6);
+    MARK(7);
   }
-  MARK(7);
+  MARK(8);
 #undef MARK
   if (launches) *launches = nl;
   return EIG_OK;
@@ -371,10 +403,11 @@ int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* strea
   const bool report = (P->want & EIG_REPORT) != 0 && vectors;
   eig_problem Pe = *P;
   if (!report) Pe.want &= ~EIG_REPORT;
-  const size_t need = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report).bytes;
+  const bool mixed = h->mode == EIG_MIXED;
+  const size_t need = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report, mixed).bytes;
   rc = ensure_ws(h, need);
   if (rc) return rc;
-  Carve c = plan(h->ws, P->n, P->k, vectors, P->Q_out == nullptr, report);
+  Carve c = plan(h->ws, P->n, P->k, vectors, P->Q_out == nullptr, report, mixed);
   rc = enqueue_update(h, &Pe, c, s, negmask, kplus, rep ? h->ev : nullptr, &h->last_launches);
   if (rc) return rc;
   h->last_stream = s;
@@ -400,13 +433,14 @@ int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* strea
       }
       return ms;
     };
-    rep->ms_total = span(0, 7);
+    rep->ms_total = span(0, 8);
     rep->ms_project = span(0, 1);
     rep->ms_deflate = span(1, 2);
     rep->ms_counts = span(2, 3);
     rep->ms_roots = span(3, 4);
     rep->ms_assemble = span(4, 5);
-    rep->ms_gemm = span(5, 6);
+    rep->ms_slice = span(5, 6);
+    rep->ms_gemm = span(6, 7);
     rep->launches = h->last_launches;
   }
   return status;
@@ -426,7 +460,7 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
     if (P->n < 1 || P->k < 1) continue;
     const bool vectors = (P->want & EIG_VECTORS) != 0;
     const bool report = (P->want & EIG_REPORT) != 0 && vectors;
-    size_t b = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report).bytes;
+    size_t b = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report, h->mode == EIG_MIXED).bytes;
     if (b > need) need = b;
   }
   int rc = ensure_ws(h, need);
@@ -453,7 +487,7 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
       return EIG_ENOMEM;
     }
     if (t.pre_status == EIG_OK) {
-      Carve c = plan(h->ws, Pe.n, Pe.k, vectors, Pe.Q_out == nullptr, t.report);
+      Carve c = plan(h->ws, Pe.n, Pe.k, vectors, Pe.Q_out == nullptr, t.report, h->mode == EIG_MIXED);
       int nl = 0;
       t.pre_status = enqueue_update(h, &Pe, c, s, negmask, kplus, nullptr, &nl);
       if (t.pre_status == EIG_OK) {
@@ -531,8 +565,9 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       if (!P || !out || out_bytes < sizeof(uint64_t) || P->n < 1 || P->k < 1 || P->k > EIG_MAX_K)
         return EIG_EINVAL;
       const bool vectors = (P->want & EIG_VECTORS) != 0;
-      *static_cast<uint64_t*>(out) =
-          plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, (P->want & EIG_REPORT) && vectors).bytes;
+      *static_cast<uint64_t*>(out) = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr,
+                                          (P->want & EIG_REPORT) && vectors, h->mode == EIG_MIXED)
+                                         .bytes;
       return EIG_OK;
     }
     case EIG_Q_COUNT: {

@@ -2,7 +2,9 @@
 // launch wrappers).  Everything here belongs to the product library only.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/eig_update.h"
@@ -28,6 +30,7 @@ enum : int {
   ST_UNSORTED = 1,
   ST_NONFINITE = 2,
   ST_NOTCONV = 4,
+  ST_TIMEOUT = 8,
 };
 
 // Per-update device status block (one cache line).
@@ -70,6 +73,38 @@ struct RootOut {
   int* sidx;        // 2 per root: indices of the bracketing poles (-1: none)
 };
 
+// ---- split-BF16 tensor-core GEMM (gemm_tc.cu) ------------------------------
+constexpr int kTcSlices = 5;
+
+// Exponent e with |v| < 2^(e-1) for mx = max |v| (0 for an all-zero vector).
+__device__ __forceinline__ int tc_scale_exp(double mx) {
+  if (!(mx > 0.0)) return 0;
+  int E;
+  frexp(mx, &E);  // mx = f 2^E, f in [1/2, 1)
+  return E + 1;
+}
+
+// Five balanced 8-bit digits of r (|r| < 1/2): slice p holds m_p 2^(-8p) with
+// m_p = rint(256 t_p), t_{p+1} = 256 t_p - m_p, |m_p| <= 128 (exact in BF16).
+__device__ __forceinline__ void tc_split(double r, __nv_bfloat16 (&out)[kTcSlices]) {
+  double t = r;
+#pragma unroll
+  for (int p = 0; p < kTcSlices; ++p) {
+    const double m = rint(t * 256.0);
+    t = t * 256.0 - m;
+    out[p] = __double2bfloat16(ldexp(m, -8 * p));
+  }
+}
+
+// W written directly as slices (mixed mode): Ws[q][r][j] for W[j, r], leading
+// dimension lds, plane stride `plane`; fcol[r] = column exponent.
+struct WSlices {
+  __nv_bfloat16* Ws = nullptr;
+  size_t plane = 0;
+  int lds = 0;
+  int* fcol = nullptr;
+};
+
 // ---- launch wrappers (defined in the .cu files) ----------------------------
 cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* K, double* U,
                                cudaStream_t s);
@@ -88,7 +123,8 @@ cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int*
 // of W (n x n, column-major, zero-filled beforehand by the caller).
 cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
                             const double* lam_defl, const DevStatus* st, double* mu_sec,
-                            double* lam_out, double* W, cudaStream_t s);
+                            double* lam_out, double* W, cudaStream_t s,
+                            const WSlices& ws = WSlices());
 cudaError_t launch_gemm_f64(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                             const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 // Same, but skipped on the device when st reports invalid input.
@@ -111,5 +147,19 @@ cudaError_t launch_check_pairs(int64_t n, int k, const double* Q, const double* 
                                const double* K, unsigned long long negmask, const double* X,
                                const double* mu, const int* cols, int ncols, double* tmp,
                                double* out, cudaStream_t s);
+
+
+// Slice arrays hold tc_num_slices() planes of n rows x tc_slice_ld(n) BF16.
+int tc_slice_ld(int n);
+size_t tc_slice_plane(int n);
+int tc_num_slices();
+// Row exponents and slices of Q (column-major FP64).  rmax: n u64 scratch.
+cudaError_t launch_slice_q(int n, const double* Q, unsigned long long* rmax, int* erow,
+                           __nv_bfloat16* Qs, const DevStatus* st, cudaStream_t s);
+// X (column-major, ldx) = 2^(e_i+f_r-16) sum_{p+q<=6} Qs_p Ws_q^T.  err: status word
+// that receives ST_TIMEOUT if a bounded wait gave up.
+cudaError_t launch_gemm_tc(int n, const __nv_bfloat16* Qs, const __nv_bfloat16* Ws, const int* erow,
+                           const int* fcol, double* X, int ldx, const DevStatus* st, int* err,
+                           cudaStream_t s);
 
 }  // namespace eig

@@ -635,7 +635,7 @@ __global__ void mu_kernel(Sub sub, RootOut roots, double* __restrict__ mu_sec) {
 __global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_defl,
                                 const double* __restrict__ lam_defl, const DevStatus* st,
                                 const double* __restrict__ mu_sec, double* __restrict__ lam_out,
-                                double* __restrict__ W) {
+                                double* __restrict__ W, WSlices ws) {
   if (input_invalid(st)) return;
   const int nk = *sub.n_dev;
   const int nd = st->n_defl;
@@ -644,6 +644,10 @@ __global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_
     const int64_t pos = j + upper_bound_d(mu_sec, nk, v);
     lam_out[pos] = v;
     if (W) W[(int64_t)idx_defl[j] + pos * n] = 1.0;
+    if (ws.Ws) {  // e_i: 1 = 2^(f-8) * 64 with f = 2
+      ws.Ws[(size_t)pos * ws.lds + idx_defl[j]] = __double2bfloat16(64.0);
+      ws.fcol[pos] = 2;
+    }
   }
 }
 
@@ -654,7 +658,8 @@ constexpr int kAsmThreads = 256;
 template <int K>
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
     Sub sub, RootOut roots, int64_t n, const double* __restrict__ lam_defl, const DevStatus* st,
-    const double* __restrict__ mu_sec, double* __restrict__ lam_out, double* __restrict__ W) {
+    const double* __restrict__ mu_sec, double* __restrict__ lam_out, double* __restrict__ W,
+    WSlices ws) {
   __shared__ double s_n2[kAsmThreads];
   __shared__ double s_mx[kAsmThreads];
   __shared__ int s_ix[kAsmThreads];
@@ -666,7 +671,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
     const double mu = mu_sec[m];
     const int64_t pos = m + lower_bound_d(lam_defl, nd, mu);
     if (t == 0) lam_out[pos] = mu;
-    if (!W) continue;
+    if (!W && !ws.Ws) continue;
     const int o = roots.origin[m];
     const double tau = roots.tau[m];
     const double lam_o = sub.lam[o];
@@ -715,8 +720,22 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
     __syncthreads();
     const double wmax = wcomp(imax);
     const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
-    double* col = W + pos * n;
-    for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+    if (W) {
+      double* col = W + pos * n;
+      for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+    } else {
+      // Mixed mode: the column goes straight into its BF16 digit slices.
+      const int f = tc_scale_exp(fabs(wmax * scale));
+      if (t == 0) ws.fcol[pos] = f;
+      __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
+      for (int i = t; i < nk; i += kAsmThreads) {
+        __nv_bfloat16 d[kTcSlices];
+        tc_split(ldexp(wcomp(i) * scale, -f), d);
+        const int j = sub.idx[i];
+#pragma unroll
+        for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
+      }
+    }
   }
 }
 
@@ -755,14 +774,16 @@ cudaError_t launch_roots_k(const Sub& sub, const int* pole_cnt, int max_iter, in
 template <int K>
 cudaError_t launch_assemble_k(const Sub& sub, const RootOut& roots, int64_t n,
                               const int* idx_defl, const double* lam_defl, const DevStatus* st,
-                              double* mu_sec, double* lam_out, double* W, cudaStream_t s) {
+                              double* mu_sec, double* lam_out, double* W, cudaStream_t s,
+                              const WSlices& ws) {
   const int ld = sub.ld;
   mu_kernel<<<(ld + 255) / 256, 256, 0, s>>>(sub, roots, mu_sec);
   int blocks = ld < 65535 ? ld : 65535;
-  assemble_kernel<K><<<blocks, kAsmThreads, 0, s>>>(sub, roots, n, lam_defl, st, mu_sec, lam_out, W);
+  assemble_kernel<K><<<blocks, kAsmThreads, 0, s>>>(sub, roots, n, lam_defl, st, mu_sec, lam_out, W,
+                                                     ws);
   int nb = (int)((n + 255) / 256);
   if (nb > 4096) nb = 4096;
-  deflated_kernel<<<nb, 256, 0, s>>>(sub, n, idx_defl, lam_defl, st, mu_sec, lam_out, W);
+  deflated_kernel<<<nb, 256, 0, s>>>(sub, n, idx_defl, lam_defl, st, mu_sec, lam_out, W, ws);
   return cudaGetLastError();
 }
 
@@ -798,9 +819,9 @@ cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int*
 
 cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
                             const double* lam_defl, const DevStatus* st, double* mu_sec,
-                            double* lam_out, double* W, cudaStream_t s) {
+                            double* lam_out, double* W, cudaStream_t s, const WSlices& ws) {
   switch (sub.K) {
-#define A_(K_) case K_: return launch_assemble_k<K_>(sub, roots, n, idx_defl, lam_defl, st, mu_sec, lam_out, W, s);
+#define A_(K_) case K_: return launch_assemble_k<K_>(sub, roots, n, idx_defl, lam_defl, st, mu_sec, lam_out, W, s, ws);
     A_(1) A_(2) A_(3) A_(4) A_(5) A_(6) A_(7) A_(8) A_(10) A_(12) A_(14) A_(16)
 #undef A_
     default: return cudaErrorInvalidValue;

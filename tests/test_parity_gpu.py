@@ -261,3 +261,45 @@ def test_batch_matches_solo(eu, handle):
         solo_rc, _, mu_s, X_s = _run_update(eu, handle, P, want=eu.EIG_VALUES | eu.EIG_VECTORS)
         assert np.array_equal(host(d["lam"]), mu_s)
         assert np.array_equal(host(d["Q"]), X_s)
+
+
+# ---------------------------------------------------------------------------
+# Mixed mode: X = Q W as split-BF16 tensor-core products (5 slices, 15 pairs)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def handle_mixed(eu):
+    h = eu.eig_update_init(0, eu.EIG_MIXED)
+    yield h
+    eu.eig_update_destroy(h)
+
+
+@pytest.mark.parametrize("n,k,sigma", [(1, 1, "psd"), (100, 2, "mixed"), (256, 8, "psd"), (333, 16, "mixed"),
+                                       (1000, 5, "nsd"), (2100, 8, "mixed")])
+def test_mixed_matches_fp64_and_oracle(eu, handle, handle_mixed, n, k, sigma):
+    P = workloads.general(n, k, seed=900 + n + k, sigma=sigma, lam_kind="logspec" if n > 500 else "uniform")
+    rc, rep, mu64, X64 = _run_update(eu, handle, P, want=eu.EIG_VALUES | eu.EIG_VECTORS)
+    assert rc == 0
+    rc, rep, mum, Xm = _run_update(eu, handle_mixed, P)
+    assert rc == 0 and rep["status"] == 0
+    # the secular stage is the same FP64 path in both modes
+    assert np.array_equal(mum, mu64)
+    # X from the tensor cores vs the FP64 GEMM: 5 slices keep ~2^-40 of the scale
+    assert np.max(np.abs(Xm - X64)) <= 1e-10
+    _check_full(P, mum, Xm)
+    assert rep["max_orth"] <= 1e-10
+
+
+def test_mixed_full_size_sampled(eu, handle_mixed):
+    P = workloads.general_rank_k(k=8, seed=2000, n=8192, device="cuda:0")
+    rc, rep, mu, X = _run_update(eu, handle_mixed, P)
+    assert rc == 0
+    n = 8192
+    sel = np.unique(np.concatenate([[0, n // 3, n - 1], np.random.default_rng(6).choice(n, 29, replace=False)]))
+    ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], sel=sel)
+    scale = norm2_A(P["lam"], P["K"])
+    pos = ref["pos"]
+    assert np.max(np.abs(mu[pos] - ref["mu"])) <= MU_TOL * scale
+    assert np.min(cos_match(X[:, pos], ref["X"])) >= 1 - 1e-9
+    res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu[pos], X[:, pos])
+    assert np.max(res) <= RES_TOL * scale
+    assert rep["max_residual"] <= RES_TOL * scale and rep["max_orth"] <= 1e-10
