@@ -185,9 +185,9 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
 // symmetric 2x2 Schur decomposition; lane r applies it to row/column r.
 // ----------------------------------------------------------------------------
 template <int K>
-__device__ void warp_jacobi(double* A, double* V, int lane) {
+__device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) {
   constexpr int KP = K + 1;
-  if (V) {
+  if (V && init_v) {
     for (int idx = lane; idx < K * K; idx += 32) {
       const int r = idx / K, c = idx - (idx / K) * K;
       V[r * KP + c] = (r == c) ? 1.0 : 0.0;
@@ -489,9 +489,39 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
           Z[r * ZP + c] = v;
         }
         __syncwarp();
-        warp_jacobi<Z2>(Z, V, lane);
-        // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]).
-        double zj = 0.0, contrib = 0.0;
+        if (it > 0) {
+          // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
+          // then let Jacobi finish and accumulate onto V.
+          double zv[Z2];
+          if (lane < Z2) {
+#pragma unroll
+            for (int r = 0; r < Z2; ++r) {
+              double acc = 0.0;
+              for (int c = 0; c < Z2; ++c) acc = fma(Z[r * ZP + c], V[c * ZP + lane], acc);
+              zv[r] = acc;
+            }
+          }
+          __syncwarp();
+          if (lane < Z2) {
+            for (int i = 0; i < Z2; ++i) {
+              double acc = 0.0;
+#pragma unroll
+              for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], zv[r], acc);
+              Z[i * ZP + lane] = acc;
+            }
+          }
+          __syncwarp();
+          if (lane < Z2) {  // exact symmetry
+            for (int i = lane + 1; i < Z2; ++i) Z[i * ZP + lane] = Z[lane * ZP + i];
+          }
+          __syncwarp();
+          warp_jacobi<Z2>(Z, V, lane, false);
+        } else {
+          warp_jacobi<Z2>(Z, V, lane, true);
+        }
+        // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]);
+        // G = (Z^{-1})_{SS} for the two-pole model below.
+        double zj = 0.0, contrib = 0.0, g11 = 0.0, g12 = 0.0, g22 = 0.0;
         if (lane < Z2) {
           zj = Z[lane * ZP + lane];
           double q = 0.0;
@@ -500,12 +530,20 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
             for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
             q = fma(V[a * ZP + lane], na, q);
           }
-          if (has_a) q = fma(V[K * ZP + lane], V[K * ZP + lane], q);
-          if (has_b) q = fma(V[(K + 1) * ZP + lane], V[(K + 1) * ZP + lane], q);
-          contrib = q / zj;
+          const double za = V[K * ZP + lane], zb = V[(K + 1) * ZP + lane];
+          if (has_a) q = fma(za, za, q);
+          if (has_b) q = fma(zb, zb, q);
+          const double rz = 1.0 / zj;
+          contrib = q * rz;
+          g11 = za * za * rz;
+          g12 = za * zb * rz;
+          g22 = zb * zb * rz;
         }
         const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
         const double tsum = warp_sum(contrib);
+        g11 = warp_sum(g11);
+        g12 = warp_sum(g12);
+        g22 = warp_sum(g22);
         const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
         const int count = below + __popc(posmask) - posD - sub.kplus;
         ++it;
@@ -528,14 +566,55 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
             o = p;
           }
         }
+        // Two-pole model: freeze B^ (Sigma - M without the bracketing terms); then
+        // det Z = 0 becomes det(diag(x - lam_a, x - lam_b) - C) = 0 with
+        // C = U_S^T B^{-1} U_S = D_S - G^{-1}: the roots are the eigenvalues of
+        // diag(lam_a, lam_b) + C, exact in both poles.
+        double cand0 = NAN, cand1 = NAN;  // model roots inside the bracket, ascending
+        int ncand = 0;
+        {
+          const double det = g11 * g22 - g12 * g12;
+          if (isfinite(det) && det != 0.0) {
+            const double c11 = Da - g22 / det, c22 = Db - g11 / det, c12 = g12 / det;
+            if (has_a && has_b) {
+              const double t11 = da + c11, t22 = db + c22;
+              const double mid2 = 0.5 * (t11 + t22), hd = 0.5 * (t11 - t22);
+              const double rad = sqrt(hd * hd + c12 * c12);
+              const double lo2 = mid2 - rad, hi2 = mid2 + rad;
+              if (lo2 > tl && lo2 < th) {
+                cand0 = lo2;
+                ncand = 1;
+              }
+              if (hi2 > tl && hi2 < th && hi2 != lo2) {
+                if (ncand == 0) cand0 = hi2; else cand1 = hi2;
+                ++ncand;
+              }
+            } else {
+              const double t1 = has_a ? da + c11 : db + c22;
+              if (t1 > tl && t1 < th) {
+                cand0 = t1;
+                ncand = 1;
+              }
+            }
+          }
+        }
         bool conv = false, newton = false;
         double tn = tau;
-        if (c_hi - c_lo == 1) {
+        const int inb = c_hi - c_lo;  // roots in the bracket
+        const int r_in = m - c_lo;    // our root's rank among them
+        double model = NAN;
+        if (ncand > 0) {
+          if (inb == ncand) model = (r_in >= 1 && ncand == 2) ? cand1 : cand0;
+          else if (inb == 1) model = cand0;
+        }
+        if (inb == 1) {
           const double step = -1.0 / tsum;
           tn = tau + step;
           if (step == 0.0) {
             conv = true;
             tn = tau;
+          } else if (it <= 2 && isfinite(model)) {
+            tn = model;  // early steps: the model captures both poles globally
           } else if (isfinite(tn) && tn > tl && tn < th) {
             newton = true;
             if (fabs(step) <= 2.0 * kEps * fabs(tn)) conv = true;
@@ -545,9 +624,15 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
               newton = false;
               slow = 0;
             }
+          } else if (isfinite(model)) {
+            tn = model;
+          } else {
+            tn = NAN;
           }
+        } else {
+          tn = isfinite(model) ? model : NAN;
         }
-        if (!conv && !newton) {
+        if (!conv && !newton && !(tn > tl && tn < th)) {
           tn = tl + 0.5 * (th - tl);
           if (tl > 0.0 && th > 64.0 * tl) tn = sqrt(tl) * sqrt(th);
           else if (th < 0.0 && tl < 64.0 * th) tn = -(sqrt(-tl) * sqrt(-th));
