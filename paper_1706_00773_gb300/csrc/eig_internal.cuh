@@ -84,16 +84,31 @@ __device__ __forceinline__ int tc_scale_exp(double mx) {
   return E + 1;
 }
 
-// Five balanced 8-bit digits of r (|r| < 1/2): slice p holds m_p 2^(-8p) with
-// m_p = rint(256 t_p), t_{p+1} = 256 t_p - m_p, |m_p| <= 128 (exact in BF16).
-__device__ __forceinline__ void tc_split(double r, __nv_bfloat16 (&out)[kTcSlices]) {
-  double t = r;
+// Five balanced 8-bit digits of a scaled value.  R = rint(y * 2^40) is formed
+// exactly with one FMA against the constant 1.5 * 2^52 (valid while
+// |y 2^40| < 2^51), then peeled into base-256 digits m_4..m_0 in [-128, 128]
+// (least significant first, each digit chosen in [-128, 127] and the carry
+// shifted up), so that y = 2^-8 sum_p m_p 2^(-8p) up to 2^-41.  Slice p holds
+// m_p 2^(-8p) (exact in BF16).  tc_split_scaled takes x and the exact power-of-
+// two factor s with y = x * s, so the product is rounded only once.
+__device__ __forceinline__ void tc_split_scaled(double x, double s, __nv_bfloat16 (&out)[kTcSlices]) {
+  const double magic = 6755399441055744.0;  // 1.5 * 2^52
+  long long R = __double_as_longlong(fma(x, s * 1099511627776.0, magic)) - __double_as_longlong(magic);
+  int m[kTcSlices];
 #pragma unroll
-  for (int p = 0; p < kTcSlices; ++p) {
-    const double m = rint(t * 256.0);
-    t = t * 256.0 - m;
-    out[p] = __double2bfloat16(ldexp(m, -8 * p));
+  for (int p = kTcSlices - 1; p > 0; --p) {
+    int d = (int)(R & 255);
+    if (d >= 128) d -= 256;
+    m[p] = d;
+    R = (R - d) >> 8;
   }
+  m[0] = (int)R;
+#pragma unroll
+  for (int p = 0; p < kTcSlices; ++p) out[p] = __float2bfloat16_rn(ldexpf((float)m[p], -8 * p));
+}
+
+__device__ __forceinline__ void tc_split(double r, __nv_bfloat16 (&out)[kTcSlices]) {
+  tc_split_scaled(r, 1.0, out);
 }
 
 // W written directly as slices (mixed mode): Ws[q][r][j] for W[j, r], leading

@@ -418,7 +418,7 @@ __global__ void slice_q_kernel(int n, const double* __restrict__ Q,
     __nv_bfloat16 d[kSlices];
     if (i < n && j < n) {
       const int e = tc_scale_exp(__longlong_as_double((long long)rmax[i]));
-      tc_split(ldexp(Q[(size_t)j * n + i], -e), d);
+      tc_split_scaled(Q[(size_t)j * n + i], ldexp(1.0, -e), d);
       if (j == 0) erow[i] = e;
     } else {
 #pragma unroll

@@ -115,16 +115,18 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
       // Terms skip_a / skip_b (the poles bracketing a root) are left out of the
       // sums; the caller carries them exactly in a bordered matrix.
       const double r = (i == skip_a || i == skip_b) ? 0.0 : 1.0 / d;
+      // t = r u: M += t u^T, N += t t^T (= r^2 u u^T).
+      double t[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) t[c] = u[c] * r;
       int s = 0;
 #pragma unroll
       for (int a = 0; a < K; ++a) {
         if (owner_of<K, E>(a) == e) {
-          const double ta = u[a] * r;
-          const double tta = ta * r;
 #pragma unroll
           for (int b = a; b < K; ++b) {
-            A[s] = fma(ta, u[b], A[s]);
-            if (MODE == ACC_MN) B[s] = fma(tta, u[b], B[s]);
+            A[s] = fma(t[a], u[b], A[s]);
+            if (MODE == ACC_MN) B[s] = fma(t[a], t[b], B[s]);
             ++s;
           }
         }
@@ -618,6 +620,10 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
           } else if (isfinite(tn) && tn > tl && tn < th) {
             newton = true;
             if (fabs(step) <= 2.0 * kEps * fabs(tn)) conv = true;
+            // Quadratic regime confirmed (step far below the previous one): the
+            // next error is ~ step^2, below rounding, so accept without
+            // another evaluation.
+            if (fabs(step) <= 1e-10 * fabs(tn) && fabs(step) <= 1e-2 * fabs(prev_step)) conv = true;
             if (fabs(step) > 0.5 * fabs(prev_step)) ++slow; else slow = 0;
             prev_step = step;
             if (slow >= 3 && !conv) {
@@ -813,9 +819,10 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
       const int f = tc_scale_exp(fabs(wmax * scale));
       if (t == 0) ws.fcol[pos] = f;
       __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
+      const double s2 = ldexp(scale, -f);  // exact: scale * 2^-f
       for (int i = t; i < nk; i += kAsmThreads) {
         __nv_bfloat16 d[kTcSlices];
-        tc_split(ldexp(wcomp(i) * scale, -f), d);
+        tc_split_scaled(wcomp(i), s2, d);
         const int j = sub.idx[i];
 #pragma unroll
         for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
