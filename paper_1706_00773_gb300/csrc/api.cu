@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -200,87 +201,292 @@ bool sigma_info(const int8_t* sigma, int k, unsigned long long* negmask, int* kp
     }                                 \
   } while (0)
 
-// Stages a2-a9 (+ the optional check) of one update, stream-ordered.  With
-// ev != nullptr, events 0..8 are recorded at the stage boundaries.
-int enqueue_update(eig_ctx* h, const eig_problem* P, const Carve& c, cudaStream_t s,
-                   unsigned long long negmask, int kplus_k, cudaEvent_t* ev, int* launches) {
+// ---------------------------------------------------------------------------
+// A table of updates and its workspace.  Every stage of every update of the
+// table runs in one launch (one per padded rank K for the secular kernels):
+// the device reads the ProbDesc table and per-stage prefix sums of the work.
+// ---------------------------------------------------------------------------
+struct TableItem {
+  const eig_problem* P;
+  unsigned long long negmask;
+  int kplus;
+  bool report;
+};
+
+struct Bump {
+  char* base;
+  size_t off = 0;
+  explicit Bump(char* b) : base(b) {}
+  char* take(size_t bytes, size_t align = 256) {
+    off = align_up(off, align);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+struct Table {
+  // device pointers into the workspace
+  ProbDesc* d_desc = nullptr;
+  int* d_ids = nullptr;
+  long long* d_colpre = nullptr;
+  int* d_rbpre = nullptr;
+  int* d_slpre = nullptr;
+  int* d_gtpre = nullptr;
+  long long* d_cppre = nullptr;
+  void* d_maps = nullptr;
+  DevStatus* d_st = nullptr;
+  double* d_W = nullptr;
+  size_t W_bytes = 0;
+  __nv_bfloat16* d_Ws = nullptr;
+  size_t Ws_bytes = 0;
+  unsigned long long* d_rmax = nullptr;
+  size_t rmax_bytes = 0;
+  std::vector<ClassDesc> classes;
+  std::vector<int> class_items;  // sum of n per class (grid bound)
+  long long total_cols = 0, total_copy = 0;
+  int total_rb = 0, total_sl = 0, total_gt = 0;
+  // report (single update only)
+  double* chk_tmp = nullptr;
+  double* chk_out = nullptr;
+  int* chk_cols = nullptr;
+  size_t table_bytes = 0;  // size of the packed host image
+  size_t bytes = 0;        // workspace bytes
+};
+
+// Lays out (base == nullptr: sizes only) or builds the table.  host_img
+// receives the packed image of the table region (copied to d_desc).
+Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, bool vectors, bool mixed,
+                   std::vector<char>* host_img) {
+  Table T;
+  const int count = (int)items.size();
+  Bump b(base);
+  // --- table region (packed, copied from the host image in one transfer) ---
+  const size_t t0 = b.off;
+  T.d_desc = reinterpret_cast<ProbDesc*>(b.take(sizeof(ProbDesc) * count));
+  T.d_ids = reinterpret_cast<int*>(b.take(sizeof(int) * count));
+  T.d_colpre = reinterpret_cast<long long*>(b.take(sizeof(long long) * (count + 1)));
+  T.d_rbpre = reinterpret_cast<int*>(b.take(sizeof(int) * (count + 1)));
+  T.d_slpre = reinterpret_cast<int*>(b.take(sizeof(int) * (count + 1)));
+  T.d_gtpre = reinterpret_cast<int*>(b.take(sizeof(int) * (count + 1)));
+  T.d_cppre = reinterpret_cast<long long*>(b.take(sizeof(long long) * (count + 1)));
+  T.d_maps = b.take(mixed && vectors ? (size_t)128 * 2 * count : 0, 128);
+  T.table_bytes = b.off - t0;
+  // --- class scratch (device-written) ---
+  int cls_of[17];
+  for (int i = 0; i < 17; ++i) cls_of[i] = -1;
+  std::vector<int> order;  // table indices grouped by class
+  for (int K : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16}) {
+    int c = -1;
+    for (int i = 0; i < count; ++i) {
+      if (padded_rank(items[i].P->k) != K) continue;
+      if (c < 0) {
+        c = (int)T.classes.size();
+        cls_of[K] = c;
+        ClassDesc cd{};
+        cd.K = K;
+        cd.ids = T.d_ids ? T.d_ids + order.size() : nullptr;
+        T.classes.push_back(cd);
+        T.class_items.push_back(0);
+      }
+      order.push_back(i);
+      T.classes[c].count++;
+      T.class_items[c] += (int)items[i].P->n;
+    }
+  }
+  for (auto& cd : T.classes) {
+    cd.pk = reinterpret_cast<int*>(b.take(sizeof(int) * (cd.count + 1)));
+    cd.pd = reinterpret_cast<int*>(b.take(sizeof(int) * (cd.count + 1)));
+    cd.counter = reinterpret_cast<int*>(b.take(sizeof(int)));
+  }
+  // --- shared contiguous regions ---
+  T.d_st = reinterpret_cast<DevStatus*>(b.take(sizeof(DevStatus) * count));
+  size_t Wtot = 0, Wstot = 0, rtot = 0;
+  for (int i = 0; i < count; ++i) {
+    const int64_t n = items[i].P->n;
+    Wtot += sizeof(double) * (size_t)n * n;
+    Wstot += 2 * (size_t)tc_num_slices() * tc_slice_plane((int)n);
+    rtot += sizeof(unsigned long long) * (size_t)n;
+  }
+  if (vectors && !mixed) {
+    T.d_W = reinterpret_cast<double*>(b.take(Wtot));
+    T.W_bytes = Wtot;
+  }
+  if (vectors && mixed) {
+    T.d_Ws = reinterpret_cast<__nv_bfloat16*>(b.take(Wstot));
+    T.Ws_bytes = Wstot;
+    T.d_rmax = reinterpret_cast<unsigned long long*>(b.take(rtot));
+    T.rmax_bytes = rtot;
+  }
+  // --- per-update regions ---
+  std::vector<ProbDesc> desc(count);
+  std::vector<long long> colpre(count + 1, 0), cppre(count + 1, 0);
+  std::vector<int> rbpre(count + 1, 0), slpre(count + 1, 0), gtpre(count + 1, 0);
+  size_t woff = 0, wsoff = 0, roff = 0;
+  for (int i = 0; i < count; ++i) {
+    const eig_problem* P = items[i].P;
+    const int64_t n = P->n;
+    const int k = P->k;
+    const int K = padded_rank(k);
+    const size_t ld = align_up((size_t)n, 32);
+    ProbDesc& d = desc[i];
+    std::memset(&d, 0, sizeof(d));
+    d.n = (int)n;
+    d.k = k;
+    d.K = K;
+    d.ld = (int)ld;
+    d.kplus = items[i].kplus + (K - k);
+    d.negmask = items[i].negmask;
+    d.Q = P->Q;
+    d.lam = P->lambda;
+    d.Km = P->K;
+    d.st = T.d_st ? T.d_st + i : nullptr;
+    d.U = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * k));
+    d.lam_keep = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.Us = reinterpret_cast<double*>(b.take(sizeof(double) * ld * K));
+    d.idx_keep = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.idx_defl = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.lam_defl = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.pole_cnt = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.origin = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.tau = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.iters = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.rflags = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.alpha = reinterpret_cast<double*>(b.take(sizeof(double) * ld * K));
+    d.beta = reinterpret_cast<double*>(b.take(sizeof(double) * ld * 2));
+    d.sidx = reinterpret_cast<int*>(b.take(sizeof(int) * ld * 2));
+    d.mu_sec = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.lam_old = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    if (vectors) {
+      if (mixed) {
+        d.Qs = reinterpret_cast<__nv_bfloat16*>(b.take(2 * (size_t)tc_num_slices() * tc_slice_plane((int)n)));
+        d.Ws = T.d_Ws ? reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(T.d_Ws) + wsoff) : nullptr;
+        wsoff += 2 * (size_t)tc_num_slices() * tc_slice_plane((int)n);
+        d.erow = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+        d.fcol = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+        d.rmax = T.d_rmax ? reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(T.d_rmax) + roff) : nullptr;
+        roff += sizeof(unsigned long long) * (size_t)n;
+      } else {
+        d.W = T.d_W ? reinterpret_cast<double*>(reinterpret_cast<char*>(T.d_W) + woff) : nullptr;
+        woff += sizeof(double) * (size_t)n * n;
+      }
+      if (P->Q_out) {
+        d.Xout = P->Q_out;
+      } else {
+        d.Xout = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * n));
+        d.Qback = P->Q;
+      }
+    }
+    if (items[i].report && count == 1) {
+      T.chk_tmp = reinterpret_cast<double*>(b.take(sizeof(double) * 3 * (size_t)n * kCheckCols));
+      T.chk_out = reinterpret_cast<double*>(b.take(sizeof(double) * (kCheckCols + kCheckCols * kCheckCols)));
+      T.chk_cols = reinterpret_cast<int*>(b.take(sizeof(int) * kCheckCols));
+    }
+    colpre[i + 1] = colpre[i] + n;
+    rbpre[i + 1] = rbpre[i] + (int)((n + 255) / 256);
+    const int nt32 = (int)((n + 31) / 32);
+    slpre[i + 1] = slpre[i] + nt32 * nt32;
+    const int tile = mixed ? 128 : 64;
+    const int ntg = (int)((n + tile - 1) / tile);
+    gtpre[i + 1] = gtpre[i] + ntg * ntg;
+    cppre[i + 1] = cppre[i] + ((vectors && !P->Q_out) ? n * n : 0);
+  }
+  T.total_cols = colpre[count];
+  T.total_rb = rbpre[count];
+  T.total_sl = slpre[count];
+  T.total_gt = gtpre[count];
+  T.total_copy = cppre[count];
+  T.bytes = b.off;
+  if (host_img && base) {
+    host_img->assign(T.table_bytes, 0);
+    char* img = host_img->data();
+    auto put = [&](const void* dptr, const void* src, size_t bytes) {
+      if (bytes) std::memcpy(img + (reinterpret_cast<const char*>(dptr) - reinterpret_cast<const char*>(T.d_desc)), src, bytes);
+    };
+    put(T.d_desc, desc.data(), sizeof(ProbDesc) * count);
+    put(T.d_ids, order.data(), sizeof(int) * count);
+    put(T.d_colpre, colpre.data(), sizeof(long long) * (count + 1));
+    put(T.d_rbpre, rbpre.data(), sizeof(int) * (count + 1));
+    put(T.d_slpre, slpre.data(), sizeof(int) * (count + 1));
+    put(T.d_gtpre, gtpre.data(), sizeof(int) * (count + 1));
+    put(T.d_cppre, cppre.data(), sizeof(long long) * (count + 1));
+    if (mixed && vectors) {
+      for (int i = 0; i < count; ++i) {
+        char* mq = img + (reinterpret_cast<char*>(T.d_maps) - reinterpret_cast<char*>(T.d_desc)) + 256 * i;
+        if (tc_encode_map(mq, desc[i].Qs, desc[i].n) != 0 || tc_encode_map(mq + 128, desc[i].Ws, desc[i].n) != 0)
+          T.bytes = 0;  // signals failure
+      }
+    }
+  }
+  (void)h;
+  (void)cls_of;
+  return T;
+}
+
+// Stages a2-a11 (+ the optional check) of every update of the table,
+// stream-ordered.  With ev != nullptr, events 0..8 mark the stage boundaries.
+int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixed, bool report,
+                  cudaStream_t s, cudaEvent_t* ev, int* launches, const std::vector<char>& img,
+                  const eig_problem* P0, unsigned long long negmask0) {
   int nl = 0;
 #define MARK(i) \
   if (ev) CK(cudaEventRecord(ev[i], s))
-  const int64_t n = P->n;
-  const int k = P->k;
-  const int K = padded_rank(k);
-  const int ld = (int)align_up((size_t)n, 32);
-  const bool vectors = (P->want & EIG_VECTORS) != 0;
-  const bool report = (P->want & EIG_REPORT) != 0;
-  const bool mixed = vectors && h->mode == EIG_MIXED;
   MARK(0);
-  CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
-  CK(launch_project_f64(n, k, P->Q, P->K, c.U, s));
+  CK(cudaMemcpyAsync(T.d_desc, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(T.d_st, 0, sizeof(DevStatus) * count, s));
+  CK(launch_project_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
   ++nl;
-  CK(cudaMemcpyAsync(c.lam_old, P->lambda, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   MARK(1);
-  CK(launch_deflate(n, k, K, P->lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep,
-                    c.idx_defl, c.lam_defl, c.st, s));
+  CK(launch_deflate_grouped(T.d_desc, count, s));
   ++nl;
   MARK(2);
-  Sub sub;
-  sub.n_dev = &c.st->n_keep;
-  sub.ld = ld;
-  sub.K = K;
-  sub.kplus = kplus_k + (K - k);
-  sub.lam = c.lam_keep;
-  sub.Us = c.Us;
-  sub.idx = c.idx_keep;
-  sub.st = c.st;
-  sub.negmask = negmask;
-  CK(launch_counts(sub, nullptr, ld, c.pole_cnt, s));
-  ++nl;
-  MARK(3);
-  CK(cudaMemsetAsync(c.counter, 0, sizeof(int), s));
-  RootOut ro{c.origin, c.tau, c.iters, c.rflags, c.alpha, c.beta, c.sidx};
-  CK(launch_roots(sub, c.pole_cnt, h->max_iter, c.counter, ro, c.st, h->num_sms, s));
-  ++nl;
-  MARK(4);
-  WSlices ws;
-  if (mixed) {
-    ws.Ws = c.Ws;
-    ws.plane = tc_slice_plane((int)n);
-    ws.lds = tc_slice_ld((int)n);
-    ws.fcol = c.fcol;
-    CK(cudaMemsetAsync(c.Ws, 0, 2 * (size_t)tc_num_slices() * ws.plane, s));
-  } else if (vectors) {
-    CK(cudaMemsetAsync(c.W, 0, sizeof(double) * (size_t)n * n, s));
+  for (size_t c = 0; c < T.classes.size(); ++c) {
+    CK(launch_class_prefix(T.d_desc, T.classes[c], s));
+    CK(launch_counts_grouped(T.d_desc, T.classes[c], T.class_items[c], s));
+    nl += 2;
   }
-  // lam_old keeps the old eigenvalues, so the new ones go straight into lambda.
-  CK(launch_assemble(sub, ro, n, c.idx_defl, c.lam_defl, c.st, c.mu_sec, P->lambda,
-                     (vectors && !mixed) ? c.W : nullptr, s, ws));
-  nl += 3;
+  MARK(3);
+  for (size_t c = 0; c < T.classes.size(); ++c) {
+    CK(launch_roots_grouped(T.d_desc, T.classes[c], T.class_items[c], h->max_iter, h->num_sms, s));
+    ++nl;
+  }
+  MARK(4);
+  if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
+  if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
+  for (size_t c = 0; c < T.classes.size(); ++c) {
+    CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));
+    nl += 3;
+  }
   MARK(5);
   if (vectors) {
-    double* Xdst = P->Q_out ? P->Q_out : c.X;
     if (mixed) {
-      CK(launch_slice_q((int)n, P->Q, c.rmax, c.erow, c.Qs, c.st, s));
+      CK(cudaMemsetAsync(T.d_rmax, 0, T.rmax_bytes, s));
+      CK(launch_slice_q_grouped(T.d_desc, count, T.d_rbpre, T.total_rb, T.d_slpre, T.total_sl, s));
+      nl += 2;
       MARK(6);
-      CK(launch_gemm_tc((int)n, c.Qs, c.Ws, c.erow, c.fcol, Xdst, (int)n, c.st, &c.st->flags, s));
-      nl += 3;
+      CK(launch_gemm_tc_grouped(T.d_desc, count, T.d_maps, T.d_gtpre, T.total_gt, s));
+      ++nl;
     } else {
       MARK(6);
-      CK(launch_gemm_f64_guarded(n, n, n, P->Q, n, c.W, n, Xdst, n, c.st, s));
+      CK(launch_gemm_f64_grouped(T.d_desc, count, T.d_gtpre, T.total_gt, s));
       ++nl;
     }
     MARK(7);
-    if (report) {
+    if (report && count == 1) {
+      const int64_t n = P0->n;
       int cols[kCheckCols];
       const int nc = (int)(n < kCheckCols ? n : kCheckCols);
       for (int i = 0; i < nc; ++i) cols[i] = (int)((int64_t)i * (n - 1) / (nc > 1 ? nc - 1 : 1));
-      CK(cudaMemcpyAsync(c.chk_cols, cols, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-      CK(launch_check_pairs(n, k, P->Q, c.lam_old, P->K, negmask, Xdst, P->lambda, c.chk_cols, nc,
-                            c.chk_tmp, c.chk_out, s));
+      CK(cudaMemcpyAsync(T.chk_cols, cols, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+      // The check needs the old lambda and this update's X (old Q is still intact).
+      ProbDesc d0;
+      std::memcpy(&d0, img.data(), sizeof(ProbDesc));
+      CK(launch_check_pairs(n, P0->k, P0->Q, d0.lam_old, P0->K, negmask0, d0.Xout, P0->lambda,
+                            T.chk_cols, nc, T.chk_tmp, T.chk_out, s));
       nl += 6;
     }
-    if (!P->Q_out) {
-      CK(launch_copy_guarded(P->Q, c.X, n * n, c.st, s));
+    if (T.total_copy > 0) {
+      CK(launch_copyback_grouped(T.d_desc, count, T.d_cppre, T.total_copy, s));
       ++nl;
     }
   } else {
@@ -401,33 +607,34 @@ int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* strea
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool vectors = (P->want & EIG_VECTORS) != 0;
   const bool report = (P->want & EIG_REPORT) != 0 && vectors;
-  eig_problem Pe = *P;
-  if (!report) Pe.want &= ~EIG_REPORT;
   const bool mixed = h->mode == EIG_MIXED;
-  const size_t need = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report, mixed).bytes;
+  std::vector<TableItem> items{{P, negmask, kplus, report}};
+  const size_t need = layout_table(h, items, nullptr, vectors, mixed, nullptr).bytes;
   rc = ensure_ws(h, need);
   if (rc) return rc;
-  Carve c = plan(h->ws, P->n, P->k, vectors, P->Q_out == nullptr, report, mixed);
-  rc = enqueue_update(h, &Pe, c, s, negmask, kplus, rep ? h->ev : nullptr, &h->last_launches);
+  std::vector<char> img;
+  Table T = layout_table(h, items, h->ws, vectors, mixed, &img);
+  if (T.bytes == 0) return EIG_ECUDA;
+  rc = enqueue_table(h, T, 1, vectors, mixed, report, s, rep ? h->ev : nullptr, &h->last_launches, img, P,
+                     negmask);
   if (rc) return rc;
   h->last_stream = s;
+  CK(cudaMemcpyAsync(h->st_host, T.d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   if (P->want & EIG_ASYNC) {
-    CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     h->last_pending = true;
     return EIG_OK;
   }
-  CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   if (report)
-    CK(cudaMemcpyAsync(h->chk_host, c.chk_out, sizeof(double) * (kCheckCols + kCheckCols * kCheckCols),
+    CK(cudaMemcpyAsync(h->chk_host, T.chk_out, sizeof(double) * (kCheckCols + kCheckCols * kCheckCols),
                        cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   h->last_pending = false;
   const int status = status_of(*h->st_host);
   if (rep) {
     fill_report(rep, P, *h->st_host, report ? h->chk_host : nullptr, status);
-    auto span = [&](int a, int b) -> double {
+    auto span = [&](int a0, int b0) -> double {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) {
+      if (cudaEventElapsedTime(&ms, h->ev[a0], h->ev[b0]) != cudaSuccess) {
         cudaGetLastError();
         return -1.0;
       }
@@ -449,57 +656,59 @@ int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* strea
 int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* tickets,
                      void* stream) {
   if (!h || count < 0 || (count > 0 && (!probs || !tickets))) return EIG_EINVAL;
+  if (count == 0) return EIG_OK;
   DeviceGuard g(h->device);
   if (!g.ok) return EIG_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // One workspace large enough for every problem, so that no reallocation
-  // happens while earlier problems are in flight.
-  size_t need = 0;
+  const bool mixed = h->mode == EIG_MIXED;
+  // Valid problems with and without vectors form two tables (one launch
+  // sequence each); invalid ones get their status without any launch.
+  std::vector<TableItem> tab[2];
+  std::vector<int> slot[2];
+  std::vector<int> pre(count, EIG_OK);
   for (int i = 0; i < count; ++i) {
-    const eig_problem* P = &probs[i];
-    if (P->n < 1 || P->k < 1) continue;
-    const bool vectors = (P->want & EIG_VECTORS) != 0;
-    const bool report = (P->want & EIG_REPORT) != 0 && vectors;
-    size_t b = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr, report, h->mode == EIG_MIXED).bytes;
-    if (b > need) need = b;
-  }
-  int rc = ensure_ws(h, need);
-  if (rc) return rc;
-  for (int i = 0; i < count; ++i) {
-    eig_problem Pe = probs[i];
-    Ticket t;
-    t.n = Pe.n;
-    t.k = Pe.k;
     unsigned long long negmask = 0;
     int kplus = 0;
-    t.pre_status = validate(&Pe, &negmask, &kplus);
-    const bool vectors = (Pe.want & EIG_VECTORS) != 0;
-    t.report = (Pe.want & EIG_REPORT) != 0 && vectors;
-    if (!t.report) Pe.want &= ~EIG_REPORT;
+    pre[i] = validate(&probs[i], &negmask, &kplus);
+    if (pre[i] != EIG_OK) continue;
+    const int v = (probs[i].want & EIG_VECTORS) ? 1 : 0;
+    tab[v].push_back({&probs[i], negmask, kplus, false});
+    slot[v].push_back(i);
+  }
+  size_t need = 0;
+  for (int v = 0; v < 2; ++v)
+    if (!tab[v].empty()) need = std::max(need, layout_table(h, tab[v], nullptr, v == 1, mixed, nullptr).bytes);
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  std::vector<Ticket> made(count);
+  for (int i = 0; i < count; ++i) {
+    Ticket& t = made[i];
+    t.n = probs[i].n;
+    t.k = probs[i].k;
+    t.pre_status = pre[i];
     if (cudaMallocHost(&t.host, sizeof(DevStatus)) != cudaSuccess ||
         cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return EIG_ENOMEM;
     }
     std::memset(t.host, 0, sizeof(DevStatus));
-    if (t.report && cudaMallocHost(&t.chk_host, sizeof(double) * (kCheckCols + kCheckCols * kCheckCols)) != cudaSuccess) {
-      cudaGetLastError();
-      return EIG_ENOMEM;
-    }
-    if (t.pre_status == EIG_OK) {
-      Carve c = plan(h->ws, Pe.n, Pe.k, vectors, Pe.Q_out == nullptr, t.report, h->mode == EIG_MIXED);
-      int nl = 0;
-      t.pre_status = enqueue_update(h, &Pe, c, s, negmask, kplus, nullptr, &nl);
-      if (t.pre_status == EIG_OK) {
-        CK(cudaMemcpyAsync(t.host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-        if (t.report)
-          CK(cudaMemcpyAsync(t.chk_host, c.chk_out, sizeof(double) * (kCheckCols + kCheckCols * kCheckCols),
-                             cudaMemcpyDeviceToHost, s));
-      }
-    }
-    CK(cudaEventRecord(t.done, s));
-    std::lock_guard<std::mutex> lk(h->mu);
-    h->tickets.push_back(t);
+  }
+  for (int v = 0; v < 2; ++v) {
+    if (tab[v].empty()) continue;
+    std::vector<char> img;
+    Table T = layout_table(h, tab[v], h->ws, v == 1, mixed, &img);
+    if (T.bytes == 0) return EIG_ECUDA;
+    int nl = 0;
+    rc = enqueue_table(h, T, (int)tab[v].size(), v == 1, mixed, false, s, nullptr, &nl, img, nullptr, 0);
+    if (rc) return rc;
+    for (size_t j = 0; j < tab[v].size(); ++j)
+      CK(cudaMemcpyAsync(made[slot[v][j]].host, T.d_st + j, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    // The next table reuses the workspace: keep the tables stream-ordered.
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  for (int i = 0; i < count; ++i) {
+    CK(cudaEventRecord(made[i].done, s));
+    h->tickets.push_back(made[i]);
     tickets[i] = (uint64_t)h->tickets.size();  // 1-based
   }
   h->last_stream = s;

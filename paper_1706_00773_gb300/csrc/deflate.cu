@@ -72,11 +72,11 @@ __device__ __forceinline__ double row_norm2(const double* __restrict__ U, int64_
   return s;
 }
 
-__global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
+__device__ __forceinline__ void deflate_body(
     int64_t n, int k, int K, const double* __restrict__ lam, const double* __restrict__ U,
     unsigned long long negmask, double* __restrict__ lam_keep, double* __restrict__ Us, int ld,
     int* __restrict__ idx_keep, int* __restrict__ idx_defl, double* __restrict__ lam_defl,
-    DevStatus* st) {
+    DevStatus* st, double* __restrict__ lam_old) {
   __shared__ double shd[kDeflThreads];
   __shared__ int shi[kDeflThreads];
   __shared__ double colsq[EIG_MAX_K];
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
   double amax = 0.0;
   for (int64_t i = t; i < n; i += kDeflThreads) {
     const double v = lam[i];
+    if (lam_old) lam_old[i] = v;
     if (!isfinite(v)) bad |= ST_NONFINITE;
     if (i > 0 && !(lam[i - 1] <= v)) bad |= ST_UNSORTED;
     amax = fmax(amax, fabs(v));
@@ -166,7 +167,27 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
   }
 }
 
+__global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
+    int64_t n, int k, int K, const double* __restrict__ lam, const double* __restrict__ U,
+    unsigned long long negmask, double* __restrict__ lam_keep, double* __restrict__ Us, int ld,
+    int* __restrict__ idx_keep, int* __restrict__ idx_defl, double* __restrict__ lam_defl,
+    DevStatus* st) {
+  deflate_body(n, k, K, lam, U, negmask, lam_keep, Us, ld, idx_keep, idx_defl, lam_defl, st, nullptr);
+}
+
+// One CTA per update of the table.
+__global__ void __launch_bounds__(kDeflThreads) deflate_grouped_kernel(const ProbDesc* __restrict__ P) {
+  const ProbDesc& d = P[blockIdx.x];
+  deflate_body(d.n, d.k, d.K, d.lam, d.U, d.negmask, d.lam_keep, d.Us, d.ld, d.idx_keep, d.idx_defl,
+               d.lam_defl, d.st, d.lam_old);
+}
+
 }  // namespace
+
+cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s) {
+  deflate_grouped_kernel<<<count, kDeflThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const double* U,
                            unsigned long long negmask, double* lam_keep, double* Us, int ld,

@@ -120,9 +120,110 @@ struct WSlices {
   int* fcol = nullptr;
 };
 
+// ---- one update as seen by the grouped kernels -------------------------------
+// Every launch processes a table of updates (a single update is a table of
+// one).  Work items of a stage are numbered across the table; a kernel maps
+// an item to (update, local index) by binary search in a prefix array.
+struct ProbDesc {
+  int n, k, K, ld, kplus, pad_;
+  unsigned long long negmask;
+  const double* Q;   // caller: n x n old eigenvectors (column-major)
+  double* lam;       // caller: n eigenvalues, in/out
+  const double* Km;  // caller: n x k perturbation
+  double* Xout;      // n x n new eigenvectors (caller's Q_out or workspace)
+  double* Qback;     // caller's Q when the update is in place (X copied back), else null
+  double* U;
+  double* lam_keep;
+  double* Us;
+  int* idx_keep;
+  int* idx_defl;
+  double* lam_defl;
+  int* pole_cnt;
+  int* origin;
+  double* tau;
+  int* iters;
+  int* rflags;
+  double* alpha;
+  double* beta;
+  int* sidx;
+  double* mu_sec;
+  double* lam_old;
+  double* W;               // FP64 mode
+  __nv_bfloat16* Qs;       // mixed mode
+  __nv_bfloat16* Ws;
+  int* erow;
+  int* fcol;
+  unsigned long long* rmax;
+  DevStatus* st;
+};
+
+__host__ __device__ inline Sub sub_of(const ProbDesc& d) {
+  Sub s;
+  s.n_dev = &d.st->n_keep;
+  s.ld = d.ld;
+  s.K = d.K;
+  s.kplus = d.kplus;
+  s.lam = d.lam_keep;
+  s.Us = d.Us;
+  s.idx = d.idx_keep;
+  s.st = d.st;
+  s.negmask = d.negmask;
+  return s;
+}
+
+__host__ __device__ inline RootOut rootout_of(const ProbDesc& d) {
+  RootOut r;
+  r.origin = d.origin;
+  r.tau = d.tau;
+  r.iters = d.iters;
+  r.flags = d.rflags;
+  r.alpha = d.alpha;
+  r.beta = d.beta;
+  r.sidx = d.sidx;
+  return r;
+}
+
+// Index of the last prefix entry <= item (prefix[0] = 0, ascending, count+1 entries).
+template <typename T>
+__device__ __forceinline__ int find_owner(const T* prefix, int count, T item) {
+  int lo = 0, hi = count;  // answer in [0, count)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// A set of updates sharing one padded rank K (the secular kernels are
+// compiled per K).  ids: device indices into the ProbDesc table; pk / pd:
+// device prefix sums (count+1) of the kept / deflated sizes, written by
+// launch_class_prefix after deflation; counter: device work counter.
+struct ClassDesc {
+  int K;
+  int count;
+  const int* ids;
+  int* pk;
+  int* pd;
+  int* counter;
+};
+
 // ---- launch wrappers (defined in the .cu files) ----------------------------
 cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* K, double* U,
                                cudaStream_t s);
+// U = Q^T K for every update of the table; col_prefix (device, count+1): prefix
+// sums of n over the table.
+cudaError_t launch_project_grouped(const ProbDesc* P, int count, const long long* col_prefix,
+                                   long long total_cols, cudaStream_t s);
+// Deflation + compaction for every update (one CTA each); also keeps lam_old.
+cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s);
+// Prefix sums of n_keep and n_defl over a class (one small kernel).
+cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStream_t s);
+// Grouped secular stages for one class (pole counts, zero finder, assembly).
+cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s);
+cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
+                                 int num_sms, cudaStream_t s);
+cudaError_t launch_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items,
+                                    int max_defl, bool vectors, bool mixed, cudaStream_t s);
 cudaError_t launch_make_rank2(int64_t n, int64_t j, const double* a, double* K, cudaStream_t s);
 cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const double* U,
                            unsigned long long negmask, double* lam_keep, double* Us, int ld,
@@ -176,5 +277,19 @@ cudaError_t launch_slice_q(int n, const double* Q, unsigned long long* rmax, int
 cudaError_t launch_gemm_tc(int n, const __nv_bfloat16* Qs, const __nv_bfloat16* Ws, const int* erow,
                            const int* fcol, double* X, int ldx, const DevStatus* st, int* err,
                            cudaStream_t s);
+// Grouped versions over a table of updates.  Host-side prefix arrays (count+1)
+// of per-update work: row blocks of 256 (rowmax), 32x32 slice tiles, 128x128
+// GEMM tiles.  maps: device array of 2*count tensor maps (Q slices, W slices)
+// built by tc_encode_maps.
+cudaError_t launch_slice_q_grouped(const ProbDesc* P, int count, const int* rb_prefix, int total_rb,
+                                   const int* tile_prefix, int total_tiles, cudaStream_t s);
+int tc_encode_map(void* map64, const void* base, int n);  // 0 on success
+cudaError_t launch_gemm_tc_grouped(const ProbDesc* P, int count, const void* maps, const int* tile_prefix,
+                                   int total_tiles, cudaStream_t s);
+cudaError_t launch_gemm_f64_grouped(const ProbDesc* P, int count, const int* tile_prefix, int total_tiles,
+                                    cudaStream_t s);
+// X -> Q copy-back for in-place updates; elem_prefix: prefix of n*n (device).
+cudaError_t launch_copyback_grouped(const ProbDesc* P, int count, const long long* elem_prefix,
+                                    long long total, cudaStream_t s);
 
 }  // namespace eig

@@ -12,18 +12,15 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-__global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t m, int64_t n, int64_t k,
-                                                       const double* __restrict__ A, int64_t lda,
-                                                       const double* __restrict__ B, int64_t ldb,
-                                                       double* __restrict__ C, int64_t ldc,
-                                                       const DevStatus* st) {
-  if (st && (st->flags & (ST_UNSORTED | ST_NONFINITE))) return;
+__device__ __forceinline__ void gemm_f64_tile(int64_t m, int64_t n, int64_t k,
+                                              const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ B, int64_t ldb,
+                                              double* __restrict__ C, int64_t ldc, int64_t row0,
+                                              int64_t col0) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads
-  const int64_t row0 = (int64_t)blockIdx.x * BM;
-  const int64_t col0 = (int64_t)blockIdx.y * BN;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -73,7 +70,55 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t m, int64_t n, int
   }
 }
 
+__global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t m, int64_t n, int64_t k,
+                                                       const double* __restrict__ A, int64_t lda,
+                                                       const double* __restrict__ B, int64_t ldb,
+                                                       double* __restrict__ C, int64_t ldc,
+                                                       const DevStatus* st) {
+  if (st && (st->flags & (ST_UNSORTED | ST_NONFINITE))) return;
+  gemm_f64_tile(m, n, k, A, lda, B, ldb, C, ldc, (int64_t)blockIdx.x * BM, (int64_t)blockIdx.y * BN);
+}
+
+// X = Q W for every update of a table; CTA b handles tile (b - prefix[p]) of update p.
+__global__ void __launch_bounds__(256) gemm_f64_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                                               const int* __restrict__ tile_prefix) {
+  const int p = find_owner(tile_prefix, count, (int)blockIdx.x);
+  const ProbDesc& d = P[p];
+  if (d.st->flags & (ST_UNSORTED | ST_NONFINITE)) return;
+  const int tm = (d.n + BM - 1) / BM;
+  const int local = (int)blockIdx.x - tile_prefix[p];
+  gemm_f64_tile(d.n, d.n, d.n, d.Q, d.n, d.W, d.n, d.Xout, d.n, (int64_t)(local % tm) * BM,
+                (int64_t)(local / tm) * BN);
+}
+
+__global__ void copyback_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                        const long long* __restrict__ pre, long long total) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = find_owner(pre, count, e);
+    const ProbDesc& d = P[p];
+    if (!d.Qback || (d.st->flags & (ST_UNSORTED | ST_NONFINITE))) continue;
+    const long long i = e - pre[p];
+    d.Qback[i] = d.Xout[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gemm_f64_grouped(const ProbDesc* P, int count, const int* tile_prefix, int total_tiles,
+                                    cudaStream_t s) {
+  gemm_f64_grouped_kernel<<<total_tiles, 256, 0, s>>>(P, count, tile_prefix);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copyback_grouped(const ProbDesc* P, int count, const long long* elem_prefix,
+                                    long long total, cudaStream_t s) {
+  long long blocks = (total + 255) / 256;
+  if (blocks > 16384) blocks = 16384;
+  if (blocks < 1) blocks = 1;
+  copyback_grouped_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, count, elem_prefix, total);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_f64_guarded(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                                     const double* B, int64_t ldb, double* C, int64_t ldc,

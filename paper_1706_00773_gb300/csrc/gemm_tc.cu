@@ -167,9 +167,9 @@ struct GemmArgs {
   int tiles_m, tiles_n;
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapW,
-                   GemmArgs a) {
+// One 128 x 128 output tile (the whole CTA takes part).
+__device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUtensorMap* mapWp,
+                                             const GemmArgs& a, int tile) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   if (a.st && (a.st->flags & (ST_UNSORTED | ST_NONFINITE))) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_fail;
 
   // Tile raster: groups of 16 row tiles sweep the columns together (L2 reuse).
-  const int tile = blockIdx.x;
   const int group = 16;
   const int per_group = group * a.tiles_n;
   const int gi = tile / per_group;
@@ -241,9 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(bar_full0 + 8 * s, kStageBytes);
         const uint32_t st_base = sbase + s * kStageBytes;
         for (int p = 0; p < kSlices; ++p)
-          tma_load_3d(st_base + p * kTileBytes, &mapQ, kb * BK, m0, p, bar_full0 + 8 * s);
+          tma_load_3d(st_base + p * kTileBytes, mapQp, kb * BK, m0, p, bar_full0 + 8 * s);
         for (int q = 0; q < kSlices; ++q)
-          tma_load_3d(st_base + (kSlices + q) * kTileBytes, &mapW, kb * BK, n0, q,
+          tma_load_3d(st_base + (kSlices + q) * kTileBytes, mapWp, kb * BK, n0, q,
                       bar_full0 + 8 * s);
         issued = kb + 1;
       }
@@ -390,6 +389,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapW,
+                   GemmArgs a) {
+  gemm_tc_tile(&mapQ, &mapW, a, blockIdx.x);
+}
+
+// Tiles of every update of a table: CTA b handles tile (b - prefix[p]) of update
+// p; the tensor maps (Q slices, W slices per update) live in global memory.
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_grouped_kernel(const CUtensorMap* __restrict__ maps, const ProbDesc* __restrict__ P,
+                           const int* __restrict__ tile_prefix, int count) {
+  const int p = find_owner(tile_prefix, count, (int)blockIdx.x);
+  const ProbDesc& d = P[p];
+  const CUtensorMap* mq = maps + 2 * p;
+  const CUtensorMap* mw = maps + 2 * p + 1;
+  if (threadIdx.x == 0) {
+    // The maps were written by a host copy: order them for the tensor-map proxy.
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mq) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mw) : "memory");
+  }
+  GemmArgs a;
+  a.n = d.n;
+  a.ldx = d.n;
+  a.X = d.Xout;
+  a.erow = d.erow;
+  a.fcol = d.fcol;
+  a.st = d.st;
+  a.err = &d.st->flags;
+  a.tiles_m = (d.n + BM - 1) / BM;
+  a.tiles_n = a.tiles_m;
+  gemm_tc_tile(mq, mw, a, (int)blockIdx.x - tile_prefix[p]);
+}
+
 // ---- slicing ------------------------------------------------------------------
 // Row maxima of |Q| (column-major), as ordered bit patterns of non-negative doubles.
 __global__ void rowmax_kernel(int n, const double* __restrict__ Q,
@@ -437,6 +469,60 @@ __global__ void slice_q_kernel(int n, const double* __restrict__ Q,
   }
 }
 
+// Grouped versions: block b of the row-max grid covers rows of update p,
+// block b of the slice grid one 32 x 32 tile of update p.
+__global__ void rowmax_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                      const int* __restrict__ rb_prefix) {
+  const int p = find_owner(rb_prefix, count, (int)blockIdx.x);
+  const ProbDesc& d = P[p];
+  if (d.st->flags & (ST_UNSORTED | ST_NONFINITE)) return;
+  const int n = d.n;
+  const int i = ((int)blockIdx.x - rb_prefix[p]) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cols_per = (n + gridDim.y - 1) / gridDim.y;
+  const int j0 = blockIdx.y * cols_per, j1 = min(n, j0 + cols_per);
+  double m = 0.0;
+  for (int j = j0; j < j1; ++j) m = fmax(m, fabs(d.Q[(size_t)j * n + i]));
+  if (j1 > j0) atomicMax(&d.rmax[i], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void slice_q_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                       const int* __restrict__ tile_prefix) {
+  __shared__ __nv_bfloat16 tile[kSlices][32][33];
+  const int p = find_owner(tile_prefix, count, (int)blockIdx.x);
+  const ProbDesc& d = P[p];
+  if (d.st->flags & (ST_UNSORTED | ST_NONFINITE)) return;  // uniform across the CTA
+  const int n = d.n;
+  const int nt = (n + 31) / 32;
+  const int local = (int)blockIdx.x - tile_prefix[p];
+  const int i0 = (local / nt) * 32, j0 = (local % nt) * 32;
+  const int lds = (n + 63) / 64 * 64;
+  const size_t plane = (size_t)lds * (size_t)n;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = i0 + tx, j = j0 + jj;
+    __nv_bfloat16 dd[kSlices];
+    if (i < n && j < n) {
+      const int e = tc_scale_exp(__longlong_as_double((long long)d.rmax[i]));
+      tc_split_scaled(d.Q[(size_t)j * n + i], ldexp(1.0, -e), dd);
+      if (j == 0) d.erow[i] = e;
+    } else {
+#pragma unroll
+      for (int q = 0; q < kSlices; ++q) dd[q] = __double2bfloat16(0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < kSlices; ++q) tile[q][tx][jj] = dd[q];
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < n && j < n) {
+#pragma unroll
+      for (int q = 0; q < kSlices; ++q) d.Qs[(size_t)q * plane + (size_t)i * lds + j] = tile[q][ii][tx];
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 int make_map(CUtensorMap* map, const void* base, int n, int lds) {
@@ -474,6 +560,27 @@ cudaError_t launch_slice_q(int n, const double* Q, unsigned long long* rmax, int
   dim3 g2((n + 31) / 32, (n + 31) / 32);
   slice_q_kernel<<<g2, dim3(32, 8), 0, s>>>(n, Q, rmax, erow, Qs, tc_slice_plane(n), tc_slice_ld(n),
                                             st);
+  return cudaGetLastError();
+}
+
+int tc_encode_map(void* map64, const void* base, int n) {
+  return make_map(reinterpret_cast<CUtensorMap*>(map64), base, n, tc_slice_ld(n));
+}
+
+cudaError_t launch_slice_q_grouped(const ProbDesc* P, int count, const int* rb_prefix, int total_rb,
+                                   const int* tile_prefix, int total_tiles, cudaStream_t s) {
+  rowmax_grouped_kernel<<<dim3(total_rb, 64), 256, 0, s>>>(P, count, rb_prefix);
+  slice_q_grouped_kernel<<<total_tiles, dim3(32, 8), 0, s>>>(P, count, tile_prefix);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_grouped(const ProbDesc* P, int count, const void* maps, const int* tile_prefix,
+                                   int total_tiles, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBytes);
+  if (e != cudaSuccess) return e;
+  gemm_tc_grouped_kernel<<<total_tiles, kThreads, kSmemBytes, s>>>(
+      reinterpret_cast<const CUtensorMap*>(maps), P, tile_prefix, count);
   return cudaGetLastError();
 }
 

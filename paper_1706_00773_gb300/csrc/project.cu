@@ -12,12 +12,9 @@ constexpr int kProjChunk = 8;  // columns of K accumulated per pass over a Q col
 // kProjChunk columns held in registers, then reduced across the warp with a
 // fixed butterfly (deterministic).  Roofline: FP64 FMA (2 n^2 k flops against
 // n^2 * 8 bytes of Q).
-__global__ void __launch_bounds__(256) project_f64_kernel(int64_t n, int k, const double* __restrict__ Q,
-                                                          const double* __restrict__ K,
-                                                          double* __restrict__ U) {
-  const int lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= n) return;
+__device__ __forceinline__ void project_column(int64_t n, int k, const double* __restrict__ Q,
+                                               const double* __restrict__ K,
+                                               double* __restrict__ U, int64_t j, int lane) {
   const double* q = Q + j * n;
   for (int c0 = 0; c0 < k; c0 += kProjChunk) {
     double acc[kProjChunk];
@@ -40,6 +37,27 @@ __global__ void __launch_bounds__(256) project_f64_kernel(int64_t n, int k, cons
   }
 }
 
+__global__ void __launch_bounds__(256) project_f64_kernel(int64_t n, int k, const double* __restrict__ Q,
+                                                          const double* __restrict__ K,
+                                                          double* __restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  project_column(n, k, Q, K, U, j, lane);
+}
+
+// Warp w of the grid handles column (w - prefix[p]) of update p.
+__global__ void __launch_bounds__(256) project_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                                              const long long* __restrict__ pre,
+                                                              long long total) {
+  const int lane = threadIdx.x & 31;
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= total) return;
+  const int p = find_owner(pre, count, w);
+  const ProbDesc& d = P[p];
+  project_column(d.n, d.k, d.Q, d.Km, d.U, w - pre[p], lane);
+}
+
 // K = [(e_j + a)/sqrt(2), (e_j - a)/sqrt(2)]: e_j a^T + a e_j^T = K diag(1,-1) K^T.
 __global__ void make_rank2_kernel(int64_t n, int64_t j, const double* __restrict__ a,
                                   double* __restrict__ K) {
@@ -59,6 +77,13 @@ cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* 
   const int warps = 8;
   const int64_t blocks = (n + warps - 1) / warps;
   project_f64_kernel<<<(unsigned)blocks, warps * 32, 0, s>>>(n, k, Q, K, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_grouped(const ProbDesc* P, int count, const long long* col_prefix,
+                                   long long total_cols, cudaStream_t s) {
+  const long long blocks = (total_cols + 7) / 8;
+  project_grouped_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, count, col_prefix, total_cols);
   return cudaGetLastError();
 }
 

@@ -277,32 +277,16 @@ __device__ __forceinline__ double sigma_of(unsigned long long negmask, int a) {
 // with M~ the sum over the other terms.  Away from poles G = 0 and this is (1).
 // ----------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __restrict__ xs,
-                                                     int npts, int* __restrict__ counts) {
+__device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, bool absolute,
+                                            double tau, double lam_o, int* out, double* M,
+                                            double* Gm, double* Vg, double* Ev, int g, int e,
+                                            int lane) {
   constexpr int E = warps_per_root(K);
-  constexpr int G = 4 / E;
   constexpr int KP = K + 1;
-  __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
-  __shared__ double sEv[G][K];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = warp / E, e = warp - (warp / E) * E;
-  if (input_invalid(sub.st)) return;
-  const int n = *sub.n_dev;
-  const bool absolute = (xs != nullptr);
-  const int limit = absolute ? npts : n;
-  // Every group runs the same number of trips so that the named barriers match.
-  for (int base = blockIdx.x * G; base < limit; base += gridDim.x * G) {
-    const int pt = base + g;
-    const bool active = pt < limit;
-    double* M = sM[g];
-    double* Gm = sG[g];
-    int below = 0;
-    if (active) {
-      const double tau = absolute ? xs[pt] : 0.0;
-      const double lam_o = absolute ? 0.0 : sub.lam[pt];
-      below = accumulate_group<K, E, ACC_MG>(e, sub.lam, sub.Us, sub.ld, n, lam_o, absolute, tau,
-                                             -1, -1, M, Gm, lane);
-    }
+  int below = 0;
+  if (active)
+    below = accumulate_group<K, E, ACC_MG>(e, sub.lam, sub.Us, sub.ld, n, lam_o, absolute, tau,
+                                           -1, -1, M, Gm, lane);
     group_sync<E>(g);
     if (active && e == 0) {
       for (int idx = lane; idx < K * K; idx += 32) {
@@ -321,14 +305,14 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
       __syncwarp();
       int dimR = 0;
       if (gmax > 0.0) {
-        double* V = sV[g];
+        double* V = Vg;
         warp_jacobi<K>(Gm, V, lane);
-        if (lane < K) sEv[g][lane] = Gm[lane * KP + lane];
+        if (lane < K) Ev[lane] = Gm[lane * KP + lane];
         __syncwarp();
         double emax = 0.0;
-        for (int j = 0; j < K; ++j) emax = fmax(emax, sEv[g][j]);
+        for (int j = 0; j < K; ++j) emax = fmax(emax, Ev[j]);
         const double tol = 64.0 * kEps * K * emax;
-        for (int j = 0; j < K; ++j) dimR += (sEv[g][j] > tol) ? 1 : 0;
+        for (int j = 0; j < K; ++j) dimR += (Ev[j] > tol) ? 1 : 0;
         // T = V^T B V into Gm: lane j forms column j.
         double bv[K];
         if (lane < K) {
@@ -350,14 +334,14 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
         }
         __syncwarp();
         // Range directions: decouple them with diagonal -1 (never counted).
-        if (lane < K && sEv[g][lane] > tol) {
+        if (lane < K && Ev[lane] > tol) {
           for (int i = 0; i < K; ++i) {
             Gm[lane * KP + i] = 0.0;
             Gm[i * KP + lane] = 0.0;
           }
         }
         __syncwarp();
-        if (lane < K && sEv[g][lane] > tol) Gm[lane * KP + lane] = -1.0;
+        if (lane < K && Ev[lane] > tol) Gm[lane * KP + lane] = -1.0;
         __syncwarp();
         warp_jacobi<K>(Gm, nullptr, lane);
         M = Gm;
@@ -366,10 +350,70 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
       }
       const unsigned pos = __ballot_sync(0xffffffffu, lane < K && M[(lane < K ? lane : 0) * KP + (lane < K ? lane : 0)] > 0.0);
       const int cnt = below + dimR + __popc(pos) - sub.kplus;
-      if (lane == 0) counts[pt] = cnt;
+      if (lane == 0) *out = cnt;
       __syncwarp();
     }
     group_sync<E>(g);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __restrict__ xs,
+                                                     int npts, int* __restrict__ counts) {
+  constexpr int E = warps_per_root(K);
+  constexpr int G = 4 / E;
+  constexpr int KP = K + 1;
+  __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
+  __shared__ double sEv[G][K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / E, e = warp - (warp / E) * E;
+  if (input_invalid(sub.st)) return;
+  const int n = *sub.n_dev;
+  const bool absolute = (xs != nullptr);
+  const int limit = absolute ? npts : n;
+  // Every group runs the same number of trips so that the named barriers match.
+  for (int base = blockIdx.x * G; base < limit; base += gridDim.x * G) {
+    const int pt = base + g;
+    const bool active = pt < limit;
+    const double tau = (active && absolute) ? xs[pt] : 0.0;
+    const double lam_o = (active && !absolute) ? sub.lam[pt] : 0.0;
+    count_point<K>(sub, n, active, absolute, tau, lam_o, active ? counts + pt : nullptr, sM[g],
+                   sG[g], sV[g], sEv[g], g, e, lane);
+  }
+}
+
+// Pole counts of every update of a class (items numbered across the class).
+template <int K>
+__global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __restrict__ P,
+                                                             ClassDesc c) {
+  constexpr int E = warps_per_root(K);
+  constexpr int G = 4 / E;
+  constexpr int KP = K + 1;
+  __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
+  __shared__ double sEv[G][K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / E, e = warp - (warp / E) * E;
+  const int total = c.pk[c.count];
+  for (int base = blockIdx.x * G; base < total; base += gridDim.x * G) {
+    const int item = base + g;
+    bool active = item < total;
+    Sub sub;
+    int n = 0, pt = 0;
+    int* out = nullptr;
+    double lam_o = 0.0;
+    if (active) {
+      const int p = find_owner(c.pk, c.count, item);
+      const ProbDesc& d = P[c.ids[p]];
+      sub = sub_of(d);
+      if (input_invalid(d.st)) {
+        active = false;
+      } else {
+        n = *sub.n_dev;
+        pt = item - c.pk[p];
+        lam_o = sub.lam[pt];
+        out = d.pole_cnt + pt;
+      }
+    }
+    count_point<K>(sub, n, active, false, 0.0, lam_o, out, sM[g], sG[g], sV[g], sEv[g], g, e, lane);
   }
 }
 
@@ -393,6 +437,298 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
 // cancels there.  A missing pole is a decoupled entry 1.
 // ----------------------------------------------------------------------------
 template <int K>
+__device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict__ pole_cnt,
+                                           int max_iter, const RootOut& out, DevStatus* st, int n,
+                                           int m, double* sMg, double* sNg, double* sZg,
+                                           double* sVg, double* s_tau, double* s_lamo,
+                                           int* s_done, int* s_ia, int* s_ib, int g, int e,
+                                           int lane) {
+  constexpr int E = warps_per_root(K);
+  constexpr int KP = K + 1;
+  constexpr int Z2 = K + 2;
+  constexpr int ZP = K + 3;
+  const int ld = sub.ld;
+  const double* __restrict__ lam = sub.lam;
+  const double* __restrict__ Us = sub.Us;
+  // ---- placement (warp 0 of the group; every lane holds the same state) ----
+  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, slow = 0, ia = -1, ib = -1;
+  bool has_a = false, has_b = false, first = false, notconv = false;
+  double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
+  if (e == 0) {
+    int lo = 0, hi = n;  // p = #{q : pole_cnt[q] <= m}
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (pole_cnt[mid] <= m) lo = mid + 1; else hi = mid;
+    }
+    p = lo;
+    has_a = p > 0;
+    has_b = p < n;
+    ia = has_a ? p - 1 : -1;
+    ib = has_b ? p : -1;
+    c_lo = has_a ? pole_cnt[p - 1] : 0;
+    c_hi = has_b ? pole_cnt[p] : n;
+    if (c_lo > m) c_lo = m;
+    if (c_hi <= m) c_hi = m + 1;
+    if (has_a && has_b) {
+      o = p - 1;
+      db = lam[p] - lam[p - 1];
+      tl = 0.0;
+      th = db;
+      tau = 0.5 * db;
+      first = true;
+    } else if (has_a) {
+      o = p - 1;
+      tl = 0.0;
+      th = sub.st->hi_sent - lam[o];
+      tau = 0.5 * th;
+    } else {
+      o = 0;
+      tl = sub.st->lo_sent - lam[0];
+      th = 0.0;
+      tau = 0.5 * tl;
+    }
+    if (lane == 0) {
+      (*s_tau) = tau;
+      (*s_lamo) = lam[o];
+      (*s_ia) = ia;
+      (*s_ib) = ib;
+    }
+  }
+  group_sync<E>(g);
+  const int skip_a = (*s_ia), skip_b = (*s_ib);
+  for (;;) {
+    const double tau_c = (*s_tau);
+    const double lam_o = (*s_lamo);
+    const int below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c,
+                                                     skip_a, skip_b, sMg, sNg, lane);
+    group_sync<E>(g);
+    if (e == 0) {
+      const double* M = sMg;
+      const double* Nm = sNg;
+      double* Z = sZg;
+      double* V = sVg;
+      const double Da = has_a ? tau - da : 1.0;
+      const double Db = has_b ? tau - db : 1.0;
+      for (int idx = lane; idx < Z2 * Z2; idx += 32) {
+        const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
+        double v;
+        if (r < K && c < K) {
+          v = ((r == c) ? sigma_of(sub.negmask, r) : 0.0) - M[r * KP + c];
+        } else if (r < K || c < K) {
+          const int row = r < K ? r : c;  // component of u
+          const int which = r < K ? c : r;  // K -> pole a, K+1 -> pole b
+          const int pi = (which == K) ? ia : ib;
+          v = (pi >= 0) ? -Us[(size_t)row * ld + pi] : 0.0;
+        } else {
+          v = (r != c) ? 0.0 : (r == K ? Da : Db);
+        }
+        Z[r * ZP + c] = v;
+      }
+      __syncwarp();
+      if (it > 0) {
+        // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
+        // then let Jacobi finish and accumulate onto V.
+        double zv[Z2];
+        if (lane < Z2) {
+#pragma unroll
+          for (int r = 0; r < Z2; ++r) {
+            double acc = 0.0;
+            for (int c = 0; c < Z2; ++c) acc = fma(Z[r * ZP + c], V[c * ZP + lane], acc);
+            zv[r] = acc;
+          }
+        }
+        __syncwarp();
+        if (lane < Z2) {
+          for (int i = 0; i < Z2; ++i) {
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], zv[r], acc);
+            Z[i * ZP + lane] = acc;
+          }
+        }
+        __syncwarp();
+        if (lane < Z2) {  // exact symmetry
+          for (int i = lane + 1; i < Z2; ++i) Z[i * ZP + lane] = Z[lane * ZP + i];
+        }
+        __syncwarp();
+        warp_jacobi<Z2>(Z, V, lane, false);
+      } else {
+        warp_jacobi<Z2>(Z, V, lane, true);
+      }
+      // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]);
+      // G = (Z^{-1})_{SS} for the two-pole model below.
+      double zj = 0.0, contrib = 0.0, g11 = 0.0, g12 = 0.0, g22 = 0.0;
+      if (lane < Z2) {
+        zj = Z[lane * ZP + lane];
+        double q = 0.0;
+        for (int a = 0; a < K; ++a) {
+          double na = 0.0;
+          for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
+          q = fma(V[a * ZP + lane], na, q);
+        }
+        const double za = V[K * ZP + lane], zb = V[(K + 1) * ZP + lane];
+        if (has_a) q = fma(za, za, q);
+        if (has_b) q = fma(zb, zb, q);
+        const double rz = 1.0 / zj;
+        contrib = q * rz;
+        g11 = za * za * rz;
+        g12 = za * zb * rz;
+        g22 = zb * zb * rz;
+      }
+      const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
+      const double tsum = warp_sum(contrib);
+      g11 = warp_sum(g11);
+      g12 = warp_sum(g12);
+      g22 = warp_sum(g22);
+      const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
+      const int count = below + __popc(posmask) - posD - sub.kplus;
+      ++it;
+      if (count <= m) {
+        tl = tau;
+        c_lo = count;
+      } else {
+        th = tau;
+        c_hi = count;
+      }
+      if (first) {
+        first = false;
+        if (count <= m) {  // root above the midpoint: measure it from pole b
+          const double sh = -db;
+          tl += sh;
+          th = 0.0;
+          tau += sh;
+          da = sh;
+          db = 0.0;
+          o = p;
+        }
+      }
+      // Two-pole model: freeze B^ (Sigma - M without the bracketing terms); then
+      // det Z = 0 becomes det(diag(x - lam_a, x - lam_b) - C) = 0 with
+      // C = U_S^T B^{-1} U_S = D_S - G^{-1}: the roots are the eigenvalues of
+      // diag(lam_a, lam_b) + C, exact in both poles.
+      double cand0 = NAN, cand1 = NAN;  // model roots inside the bracket, ascending
+      int ncand = 0;
+      {
+        const double det = g11 * g22 - g12 * g12;
+        if (isfinite(det) && det != 0.0) {
+          const double c11 = Da - g22 / det, c22 = Db - g11 / det, c12 = g12 / det;
+          if (has_a && has_b) {
+            const double t11 = da + c11, t22 = db + c22;
+            const double mid2 = 0.5 * (t11 + t22), hd = 0.5 * (t11 - t22);
+            const double rad = sqrt(hd * hd + c12 * c12);
+            const double lo2 = mid2 - rad, hi2 = mid2 + rad;
+            if (lo2 > tl && lo2 < th) {
+              cand0 = lo2;
+              ncand = 1;
+            }
+            if (hi2 > tl && hi2 < th && hi2 != lo2) {
+              if (ncand == 0) cand0 = hi2; else cand1 = hi2;
+              ++ncand;
+            }
+          } else {
+            const double t1 = has_a ? da + c11 : db + c22;
+            if (t1 > tl && t1 < th) {
+              cand0 = t1;
+              ncand = 1;
+            }
+          }
+        }
+      }
+      bool conv = false, newton = false;
+      double tn = tau;
+      const int inb = c_hi - c_lo;  // roots in the bracket
+      const int r_in = m - c_lo;    // our root's rank among them
+      double model = NAN;
+      if (ncand > 0) {
+        if (inb == ncand) model = (r_in >= 1 && ncand == 2) ? cand1 : cand0;
+        else if (inb == 1) model = cand0;
+      }
+      if (inb == 1) {
+        const double step = -1.0 / tsum;
+        tn = tau + step;
+        if (step == 0.0) {
+          conv = true;
+          tn = tau;
+        } else if (it <= 2 && isfinite(model)) {
+          tn = model;  // early steps: the model captures both poles globally
+        } else if (isfinite(tn) && tn > tl && tn < th) {
+          newton = true;
+          if (fabs(step) <= 2.0 * kEps * fabs(tn)) conv = true;
+          // Quadratic regime confirmed (step far below the previous one): the
+          // next error is ~ step^2, below rounding, so accept without
+          // another evaluation.
+          if (fabs(step) <= 1e-10 * fabs(tn) && fabs(step) <= 1e-2 * fabs(prev_step)) conv = true;
+          if (fabs(step) > 0.5 * fabs(prev_step)) ++slow; else slow = 0;
+          prev_step = step;
+          if (slow >= 3 && !conv) {
+            newton = false;
+            slow = 0;
+          }
+        } else if (isfinite(model)) {
+          tn = model;
+        } else {
+          tn = NAN;
+        }
+      } else {
+        tn = isfinite(model) ? model : NAN;
+      }
+      if (!conv && !newton && !(tn > tl && tn < th)) {
+        tn = tl + 0.5 * (th - tl);
+        if (tl > 0.0 && th > 64.0 * tl) tn = sqrt(tl) * sqrt(th);
+        else if (th < 0.0 && tl < 64.0 * th) tn = -(sqrt(-tl) * sqrt(-th));
+        if (!(tn > tl && tn < th)) {
+          conv = true;
+          tn = tl + 0.5 * (th - tl);
+        }
+        prev_step = INFINITY;
+      }
+      if (!conv && (th - tl) <= 4.0 * kEps * fmax(fabs(tl), fabs(th))) conv = true;
+      if (!conv && it >= max_iter) {
+        conv = true;
+        notconv = true;
+      }
+      tau = tn;
+      if (conv) {
+        // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
+        int jmin = 0;
+        double amin = fabs(Z[0]);
+        for (int j = 1; j < Z2; ++j) {
+          const double v = fabs(Z[j * ZP + j]);
+          if (v < amin) {
+            amin = v;
+            jmin = j;
+          }
+        }
+        if (lane < K) out.alpha[(size_t)m * K + lane] = V[lane * ZP + jmin];
+        if (lane == 0) {
+          out.beta[2 * (size_t)m] = V[K * ZP + jmin];
+          out.beta[2 * (size_t)m + 1] = V[(K + 1) * ZP + jmin];
+          out.sidx[2 * (size_t)m] = ia;
+          out.sidx[2 * (size_t)m + 1] = ib;
+          out.origin[m] = o;
+          out.tau[m] = tau;
+          out.iters[m] = it;
+          out.flags[m] = notconv ? 1 : 0;
+          atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)it);
+          atomicMax(&st->iters_max, it);
+          if (notconv) {
+            atomicAdd((unsigned long long*)&st->n_notconv, 1ull);
+            atomicOr(&st->flags, (int)ST_NOTCONV);
+          }
+        }
+      }
+      if (lane == 0) {
+        (*s_tau) = tau;
+        (*s_lamo) = lam[o];
+        (*s_done) = conv ? 1 : 0;
+      }
+    }
+    group_sync<E>(g);
+    if ((*s_done)) break;
+  }
+}
+
+template <int K>
 __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restrict__ pole_cnt,
                                                     int max_iter, int* counter, RootOut out,
                                                     DevStatus* st) {
@@ -408,290 +744,43 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
   const int n = *sub.n_dev;
-  const int ld = sub.ld;
-  const double* __restrict__ lam = sub.lam;
-  const double* __restrict__ Us = sub.Us;
   for (;;) {
     if (e == 0 && lane == 0) s_m[g] = atomicAdd(counter, 1);
     group_sync<E>(g);
     const int m = s_m[g];
     if (m >= n) break;
-    // ---- placement (warp 0 of the group; every lane holds the same state) ----
-    int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, slow = 0, ia = -1, ib = -1;
-    bool has_a = false, has_b = false, first = false, notconv = false;
-    double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
-    if (e == 0) {
-      int lo = 0, hi = n;  // p = #{q : pole_cnt[q] <= m}
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (pole_cnt[mid] <= m) lo = mid + 1; else hi = mid;
-      }
-      p = lo;
-      has_a = p > 0;
-      has_b = p < n;
-      ia = has_a ? p - 1 : -1;
-      ib = has_b ? p : -1;
-      c_lo = has_a ? pole_cnt[p - 1] : 0;
-      c_hi = has_b ? pole_cnt[p] : n;
-      if (c_lo > m) c_lo = m;
-      if (c_hi <= m) c_hi = m + 1;
-      if (has_a && has_b) {
-        o = p - 1;
-        db = lam[p] - lam[p - 1];
-        tl = 0.0;
-        th = db;
-        tau = 0.5 * db;
-        first = true;
-      } else if (has_a) {
-        o = p - 1;
-        tl = 0.0;
-        th = sub.st->hi_sent - lam[o];
-        tau = 0.5 * th;
-      } else {
-        o = 0;
-        tl = sub.st->lo_sent - lam[0];
-        th = 0.0;
-        tau = 0.5 * tl;
-      }
-      if (lane == 0) {
-        s_tau[g] = tau;
-        s_lamo[g] = lam[o];
-        s_ia[g] = ia;
-        s_ib[g] = ib;
-      }
-    }
+    root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
+                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], g, e, lane);
+  }
+}
+
+// Zero finder for every root of a class (items numbered across the class).
+template <int K>
+__global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __restrict__ P,
+                                                            ClassDesc c, int max_iter) {
+  constexpr int E = warps_per_root(K);
+  constexpr int G = 4 / E;
+  constexpr int KP = K + 1;
+  constexpr int Z2 = K + 2;
+  constexpr int ZP = K + 3;
+  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
+  __shared__ double s_tau[G], s_lamo[G];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / E, e = warp - (warp / E) * E;
+  const int total = c.pk[c.count];
+  for (;;) {
+    if (e == 0 && lane == 0) s_m[g] = atomicAdd(c.counter, 1);
     group_sync<E>(g);
-    const int skip_a = s_ia[g], skip_b = s_ib[g];
-    for (;;) {
-      const double tau_c = s_tau[g];
-      const double lam_o = s_lamo[g];
-      const int below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c,
-                                                       skip_a, skip_b, sM[g], sN[g], lane);
-      group_sync<E>(g);
-      if (e == 0) {
-        const double* M = sM[g];
-        const double* Nm = sN[g];
-        double* Z = sZ[g];
-        double* V = sV[g];
-        const double Da = has_a ? tau - da : 1.0;
-        const double Db = has_b ? tau - db : 1.0;
-        for (int idx = lane; idx < Z2 * Z2; idx += 32) {
-          const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
-          double v;
-          if (r < K && c < K) {
-            v = ((r == c) ? sigma_of(sub.negmask, r) : 0.0) - M[r * KP + c];
-          } else if (r < K || c < K) {
-            const int row = r < K ? r : c;  // component of u
-            const int which = r < K ? c : r;  // K -> pole a, K+1 -> pole b
-            const int pi = (which == K) ? ia : ib;
-            v = (pi >= 0) ? -Us[(size_t)row * ld + pi] : 0.0;
-          } else {
-            v = (r != c) ? 0.0 : (r == K ? Da : Db);
-          }
-          Z[r * ZP + c] = v;
-        }
-        __syncwarp();
-        if (it > 0) {
-          // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
-          // then let Jacobi finish and accumulate onto V.
-          double zv[Z2];
-          if (lane < Z2) {
-#pragma unroll
-            for (int r = 0; r < Z2; ++r) {
-              double acc = 0.0;
-              for (int c = 0; c < Z2; ++c) acc = fma(Z[r * ZP + c], V[c * ZP + lane], acc);
-              zv[r] = acc;
-            }
-          }
-          __syncwarp();
-          if (lane < Z2) {
-            for (int i = 0; i < Z2; ++i) {
-              double acc = 0.0;
-#pragma unroll
-              for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], zv[r], acc);
-              Z[i * ZP + lane] = acc;
-            }
-          }
-          __syncwarp();
-          if (lane < Z2) {  // exact symmetry
-            for (int i = lane + 1; i < Z2; ++i) Z[i * ZP + lane] = Z[lane * ZP + i];
-          }
-          __syncwarp();
-          warp_jacobi<Z2>(Z, V, lane, false);
-        } else {
-          warp_jacobi<Z2>(Z, V, lane, true);
-        }
-        // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]);
-        // G = (Z^{-1})_{SS} for the two-pole model below.
-        double zj = 0.0, contrib = 0.0, g11 = 0.0, g12 = 0.0, g22 = 0.0;
-        if (lane < Z2) {
-          zj = Z[lane * ZP + lane];
-          double q = 0.0;
-          for (int a = 0; a < K; ++a) {
-            double na = 0.0;
-            for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
-            q = fma(V[a * ZP + lane], na, q);
-          }
-          const double za = V[K * ZP + lane], zb = V[(K + 1) * ZP + lane];
-          if (has_a) q = fma(za, za, q);
-          if (has_b) q = fma(zb, zb, q);
-          const double rz = 1.0 / zj;
-          contrib = q * rz;
-          g11 = za * za * rz;
-          g12 = za * zb * rz;
-          g22 = zb * zb * rz;
-        }
-        const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
-        const double tsum = warp_sum(contrib);
-        g11 = warp_sum(g11);
-        g12 = warp_sum(g12);
-        g22 = warp_sum(g22);
-        const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
-        const int count = below + __popc(posmask) - posD - sub.kplus;
-        ++it;
-        if (count <= m) {
-          tl = tau;
-          c_lo = count;
-        } else {
-          th = tau;
-          c_hi = count;
-        }
-        if (first) {
-          first = false;
-          if (count <= m) {  // root above the midpoint: measure it from pole b
-            const double sh = -db;
-            tl += sh;
-            th = 0.0;
-            tau += sh;
-            da = sh;
-            db = 0.0;
-            o = p;
-          }
-        }
-        // Two-pole model: freeze B^ (Sigma - M without the bracketing terms); then
-        // det Z = 0 becomes det(diag(x - lam_a, x - lam_b) - C) = 0 with
-        // C = U_S^T B^{-1} U_S = D_S - G^{-1}: the roots are the eigenvalues of
-        // diag(lam_a, lam_b) + C, exact in both poles.
-        double cand0 = NAN, cand1 = NAN;  // model roots inside the bracket, ascending
-        int ncand = 0;
-        {
-          const double det = g11 * g22 - g12 * g12;
-          if (isfinite(det) && det != 0.0) {
-            const double c11 = Da - g22 / det, c22 = Db - g11 / det, c12 = g12 / det;
-            if (has_a && has_b) {
-              const double t11 = da + c11, t22 = db + c22;
-              const double mid2 = 0.5 * (t11 + t22), hd = 0.5 * (t11 - t22);
-              const double rad = sqrt(hd * hd + c12 * c12);
-              const double lo2 = mid2 - rad, hi2 = mid2 + rad;
-              if (lo2 > tl && lo2 < th) {
-                cand0 = lo2;
-                ncand = 1;
-              }
-              if (hi2 > tl && hi2 < th && hi2 != lo2) {
-                if (ncand == 0) cand0 = hi2; else cand1 = hi2;
-                ++ncand;
-              }
-            } else {
-              const double t1 = has_a ? da + c11 : db + c22;
-              if (t1 > tl && t1 < th) {
-                cand0 = t1;
-                ncand = 1;
-              }
-            }
-          }
-        }
-        bool conv = false, newton = false;
-        double tn = tau;
-        const int inb = c_hi - c_lo;  // roots in the bracket
-        const int r_in = m - c_lo;    // our root's rank among them
-        double model = NAN;
-        if (ncand > 0) {
-          if (inb == ncand) model = (r_in >= 1 && ncand == 2) ? cand1 : cand0;
-          else if (inb == 1) model = cand0;
-        }
-        if (inb == 1) {
-          const double step = -1.0 / tsum;
-          tn = tau + step;
-          if (step == 0.0) {
-            conv = true;
-            tn = tau;
-          } else if (it <= 2 && isfinite(model)) {
-            tn = model;  // early steps: the model captures both poles globally
-          } else if (isfinite(tn) && tn > tl && tn < th) {
-            newton = true;
-            if (fabs(step) <= 2.0 * kEps * fabs(tn)) conv = true;
-            // Quadratic regime confirmed (step far below the previous one): the
-            // next error is ~ step^2, below rounding, so accept without
-            // another evaluation.
-            if (fabs(step) <= 1e-10 * fabs(tn) && fabs(step) <= 1e-2 * fabs(prev_step)) conv = true;
-            if (fabs(step) > 0.5 * fabs(prev_step)) ++slow; else slow = 0;
-            prev_step = step;
-            if (slow >= 3 && !conv) {
-              newton = false;
-              slow = 0;
-            }
-          } else if (isfinite(model)) {
-            tn = model;
-          } else {
-            tn = NAN;
-          }
-        } else {
-          tn = isfinite(model) ? model : NAN;
-        }
-        if (!conv && !newton && !(tn > tl && tn < th)) {
-          tn = tl + 0.5 * (th - tl);
-          if (tl > 0.0 && th > 64.0 * tl) tn = sqrt(tl) * sqrt(th);
-          else if (th < 0.0 && tl < 64.0 * th) tn = -(sqrt(-tl) * sqrt(-th));
-          if (!(tn > tl && tn < th)) {
-            conv = true;
-            tn = tl + 0.5 * (th - tl);
-          }
-          prev_step = INFINITY;
-        }
-        if (!conv && (th - tl) <= 4.0 * kEps * fmax(fabs(tl), fabs(th))) conv = true;
-        if (!conv && it >= max_iter) {
-          conv = true;
-          notconv = true;
-        }
-        tau = tn;
-        if (conv) {
-          // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
-          int jmin = 0;
-          double amin = fabs(Z[0]);
-          for (int j = 1; j < Z2; ++j) {
-            const double v = fabs(Z[j * ZP + j]);
-            if (v < amin) {
-              amin = v;
-              jmin = j;
-            }
-          }
-          if (lane < K) out.alpha[(size_t)m * K + lane] = V[lane * ZP + jmin];
-          if (lane == 0) {
-            out.beta[2 * (size_t)m] = V[K * ZP + jmin];
-            out.beta[2 * (size_t)m + 1] = V[(K + 1) * ZP + jmin];
-            out.sidx[2 * (size_t)m] = ia;
-            out.sidx[2 * (size_t)m + 1] = ib;
-            out.origin[m] = o;
-            out.tau[m] = tau;
-            out.iters[m] = it;
-            out.flags[m] = notconv ? 1 : 0;
-            atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)it);
-            atomicMax(&st->iters_max, it);
-            if (notconv) {
-              atomicAdd((unsigned long long*)&st->n_notconv, 1ull);
-              atomicOr(&st->flags, (int)ST_NOTCONV);
-            }
-          }
-        }
-        if (lane == 0) {
-          s_tau[g] = tau;
-          s_lamo[g] = lam[o];
-          s_done[g] = conv ? 1 : 0;
-        }
-      }
-      group_sync<E>(g);
-      if (s_done[g]) break;
-    }
+    const int item = s_m[g];
+    if (item >= total) break;
+    const int p = find_owner(c.pk, c.count, item);
+    const ProbDesc& d = P[c.ids[p]];
+    if (input_invalid(d.st)) continue;  // uniform across the group
+    const Sub sub = sub_of(d);
+    root_solve<K>(sub, d.pole_cnt, max_iter, rootout_of(d), d.st, *sub.n_dev, item - c.pk[p],
+                  sM[g], sN[g], sZ[g], sV[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
+                  &s_ib[g], g, e, lane);
   }
 }
 
@@ -746,6 +835,86 @@ constexpr int kAsmThreads = 256;
 
 // One CTA per secular root m: w_i = (u_i^T alpha) / (lam_i - mu), |w| = 1, the
 // entry of largest magnitude made positive, scattered to W[idx_i, pos].
+// One eq. (10) column: every thread of the CTA takes part (block reductions).
+template <int K>
+__device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roots, int64_t n,
+                                              const double* __restrict__ lam_defl, int nd, int nk,
+                                              const double* __restrict__ mu_sec,
+                                              double* __restrict__ lam_out, double* __restrict__ W,
+                                              const WSlices& ws, int m, double* s_n2, double* s_mx,
+                                              int* s_ix) {
+  const int t = threadIdx.x;
+  const double mu = mu_sec[m];
+  const int64_t pos = m + lower_bound_d(lam_defl, nd, mu);
+  if (t == 0) lam_out[pos] = mu;
+  if (!W && !ws.Ws) return;
+  const int o = roots.origin[m];
+  const double tau = roots.tau[m];
+  const double lam_o = sub.lam[o];
+  const int ia = roots.sidx[2 * (size_t)m], ib = roots.sidx[2 * (size_t)m + 1];
+  const double wa = -roots.beta[2 * (size_t)m], wb = -roots.beta[2 * (size_t)m + 1];
+  double al[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) al[c] = roots.alpha[(size_t)m * K + c];
+  // eq. (10): w_i = u_i^T alpha / (lam_i - mu); the bracketing poles take -beta.
+  auto wcomp = [&](int i) -> double {
+    if (i == ia) return wa;
+    if (i == ib) return wb;
+    double ua = 0.0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) ua = fma(sub.Us[(size_t)c * sub.ld + i], al[c], ua);
+    return ua / ((sub.lam[i] - lam_o) - tau);
+  };
+  double n2 = 0.0, mx = -1.0;
+  int ix = 0x7fffffff;
+  for (int i = t; i < nk; i += kAsmThreads) {
+    const double w = wcomp(i);
+    n2 = fma(w, w, n2);
+    if (fabs(w) > mx) {
+      mx = fabs(w);
+      ix = i;
+    }
+  }
+  s_n2[t] = n2;
+  s_mx[t] = mx;
+  s_ix[t] = ix;
+  __syncthreads();
+  for (int s = kAsmThreads / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      s_n2[t] += s_n2[t + s];
+      const double om = s_mx[t + s];
+      const int oi = s_ix[t + s];
+      if (om > s_mx[t] || (om == s_mx[t] && oi < s_ix[t])) {
+        s_mx[t] = om;
+        s_ix[t] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const double nrm = sqrt(s_n2[0]);
+  const int imax = (s_ix[0] >= 0 && s_ix[0] < nk) ? s_ix[0] : 0;  // all-NaN column: any row
+  __syncthreads();
+  const double wmax = wcomp(imax);
+  const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
+  if (W) {
+    double* col = W + pos * n;
+    for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+  } else {
+    // Mixed mode: the column goes straight into its BF16 digit slices.
+    const int f = tc_scale_exp(fabs(wmax * scale));
+    if (t == 0) ws.fcol[pos] = f;
+    __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
+    const double s2 = ldexp(scale, -f);  // exact: scale * 2^-f
+    for (int i = t; i < nk; i += kAsmThreads) {
+      __nv_bfloat16 d[kTcSlices];
+      tc_split_scaled(wcomp(i), s2, d);
+      const int j = sub.idx[i];
+#pragma unroll
+      for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
+    }
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
     Sub sub, RootOut roots, int64_t n, const double* __restrict__ lam_defl, const DevStatus* st,
@@ -757,78 +926,92 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
   if (input_invalid(st)) return;
   const int nk = *sub.n_dev;
   const int nd = st->n_defl;
-  const int t = threadIdx.x;
   for (int m = blockIdx.x; m < nk; m += gridDim.x) {
-    const double mu = mu_sec[m];
-    const int64_t pos = m + lower_bound_d(lam_defl, nd, mu);
-    if (t == 0) lam_out[pos] = mu;
-    if (!W && !ws.Ws) continue;
-    const int o = roots.origin[m];
-    const double tau = roots.tau[m];
-    const double lam_o = sub.lam[o];
-    const int ia = roots.sidx[2 * (size_t)m], ib = roots.sidx[2 * (size_t)m + 1];
-    const double wa = -roots.beta[2 * (size_t)m], wb = -roots.beta[2 * (size_t)m + 1];
-    double al[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) al[c] = roots.alpha[(size_t)m * K + c];
-    // eq. (10): w_i = u_i^T alpha / (lam_i - mu); the bracketing poles take -beta.
-    auto wcomp = [&](int i) -> double {
-      if (i == ia) return wa;
-      if (i == ib) return wb;
-      double ua = 0.0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) ua = fma(sub.Us[(size_t)c * sub.ld + i], al[c], ua);
-      return ua / ((sub.lam[i] - lam_o) - tau);
-    };
-    double n2 = 0.0, mx = -1.0;
-    int ix = 0x7fffffff;
-    for (int i = t; i < nk; i += kAsmThreads) {
-      const double w = wcomp(i);
-      n2 = fma(w, w, n2);
-      if (fabs(w) > mx) {
-        mx = fabs(w);
-        ix = i;
-      }
-    }
-    s_n2[t] = n2;
-    s_mx[t] = mx;
-    s_ix[t] = ix;
+    assemble_root<K>(sub, roots, n, lam_defl, nd, nk, mu_sec, lam_out, W, ws, m, s_n2, s_mx, s_ix);
     __syncthreads();
-    for (int s = kAsmThreads / 2; s > 0; s >>= 1) {
-      if (t < s) {
-        s_n2[t] += s_n2[t + s];
-        const double om = s_mx[t + s];
-        const int oi = s_ix[t + s];
-        if (om > s_mx[t] || (om == s_mx[t] && oi < s_ix[t])) {
-          s_mx[t] = om;
-          s_ix[t] = oi;
-        }
-      }
-      __syncthreads();
-    }
-    const double nrm = sqrt(s_n2[0]);
-    const int imax = (s_ix[0] >= 0 && s_ix[0] < nk) ? s_ix[0] : 0;  // all-NaN column: any row
+  }
+}
+
+// ---- grouped assembly over a class --------------------------------------------
+__global__ void mu_grouped_kernel(const ProbDesc* __restrict__ P, ClassDesc c) {
+  const int total = c.pk[c.count];
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total;
+       item += gridDim.x * blockDim.x) {
+    const int p = find_owner(c.pk, c.count, item);
+    const ProbDesc& d = P[c.ids[p]];
+    if (input_invalid(d.st)) continue;
+    const int m = item - c.pk[p];
+    d.mu_sec[m] = d.lam_keep[d.origin[m]] + d.tau[m];
+  }
+}
+
+__device__ __forceinline__ WSlices wslices_of(const ProbDesc& d, bool mixed) {
+  WSlices ws;
+  if (mixed) {
+    ws.Ws = d.Ws;
+    ws.lds = (d.n + 63) / 64 * 64;
+    ws.plane = (size_t)ws.lds * (size_t)d.n;
+    ws.fcol = d.fcol;
+  }
+  return ws;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kAsmThreads) assemble_grouped_kernel(const ProbDesc* __restrict__ P,
+                                                                       ClassDesc c, bool vectors,
+                                                                       bool mixed) {
+  __shared__ double s_n2[kAsmThreads];
+  __shared__ double s_mx[kAsmThreads];
+  __shared__ int s_ix[kAsmThreads];
+  const int total = c.pk[c.count];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int p = find_owner(c.pk, c.count, item);
+    const ProbDesc& d = P[c.ids[p]];
+    if (input_invalid(d.st)) continue;  // uniform across the CTA
+    const Sub sub = sub_of(d);
+    const WSlices ws = wslices_of(d, vectors && mixed);
+    assemble_root<K>(sub, rootout_of(d), d.n, d.lam_defl, d.st->n_defl, *sub.n_dev, d.mu_sec, d.lam,
+                     (vectors && !mixed) ? d.W : nullptr, ws, item - c.pk[p], s_n2, s_mx, s_ix);
     __syncthreads();
-    const double wmax = wcomp(imax);
-    const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
-    if (W) {
-      double* col = W + pos * n;
-      for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
-    } else {
-      // Mixed mode: the column goes straight into its BF16 digit slices.
-      const int f = tc_scale_exp(fabs(wmax * scale));
-      if (t == 0) ws.fcol[pos] = f;
-      __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
-      const double s2 = ldexp(scale, -f);  // exact: scale * 2^-f
-      for (int i = t; i < nk; i += kAsmThreads) {
-        __nv_bfloat16 d[kTcSlices];
-        tc_split_scaled(wcomp(i), s2, d);
-        const int j = sub.idx[i];
-#pragma unroll
-        for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
-      }
+  }
+}
+
+__global__ void deflated_grouped_kernel(const ProbDesc* __restrict__ P, ClassDesc c, bool vectors,
+                                        bool mixed) {
+  const int total = c.pd[c.count];
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total;
+       item += gridDim.x * blockDim.x) {
+    const int p = find_owner(c.pd, c.count, item);
+    const ProbDesc& d = P[c.ids[p]];
+    if (input_invalid(d.st)) continue;
+    const int j = item - c.pd[p];
+    const int nk = d.st->n_keep;
+    const double v = d.lam_defl[j];
+    const int64_t pos = j + upper_bound_d(d.mu_sec, nk, v);
+    d.lam[pos] = v;
+    if (vectors && !mixed) d.W[(int64_t)d.idx_defl[j] + pos * d.n] = 1.0;
+    if (vectors && mixed) {  // e_i: 1 = 2^(f-8) * 64 with f = 2
+      const int lds = (d.n + 63) / 64 * 64;
+      d.Ws[(size_t)pos * lds + d.idx_defl[j]] = __double2bfloat16(64.0);
+      d.fcol[pos] = 2;
     }
   }
+}
+
+__global__ void class_prefix_kernel(const ProbDesc* __restrict__ P, ClassDesc c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int sk = 0, sd = 0;
+  c.pk[0] = 0;
+  c.pd[0] = 0;
+  for (int i = 0; i < c.count; ++i) {
+    const DevStatus* st = P[c.ids[i]].st;
+    const bool bad = input_invalid(st);
+    sk += bad ? 0 : st->n_keep;
+    sd += bad ? 0 : st->n_defl;
+    c.pk[i + 1] = sk;
+    c.pd[i + 1] = sd;
+  }
+  *c.counter = 0;
 }
 
 int g_occ_roots[17];
@@ -914,6 +1097,91 @@ cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, con
                             double* lam_out, double* W, cudaStream_t s, const WSlices& ws) {
   switch (sub.K) {
 #define A_(K_) case K_: return launch_assemble_k<K_>(sub, roots, n, idx_defl, lam_defl, st, mu_sec, lam_out, W, s, ws);
+    A_(1) A_(2) A_(3) A_(4) A_(5) A_(6) A_(7) A_(8) A_(10) A_(12) A_(14) A_(16)
+#undef A_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace eig
+
+// ---- grouped launchers -------------------------------------------------------
+namespace eig {
+namespace {
+
+int g_occ_roots_grouped[17];
+
+template <int K>
+cudaError_t counts_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s) {
+  constexpr int G = 4 / warps_per_root(K);
+  int blocks = (max_items + G - 1) / G;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 65535) blocks = 65535;
+  counts_grouped_kernel<K><<<blocks, 128, 0, s>>>(P, c);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t roots_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
+                            int num_sms, cudaStream_t s) {
+  constexpr int G = 4 / warps_per_root(K);
+  if (g_occ_roots_grouped[K] == 0) {
+    int occ = 0;
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, roots_grouped_kernel<K>, 128, 0);
+    if (e != cudaSuccess) return e;
+    g_occ_roots_grouped[K] = occ > 0 ? occ : 1;
+  }
+  long long want = ((long long)max_items + G - 1) / G;
+  long long cap = (long long)num_sms * g_occ_roots_grouped[K];
+  int blocks = (int)(want < cap ? want : cap);
+  if (blocks < 1) blocks = 1;
+  roots_grouped_kernel<K><<<blocks, 128, 0, s>>>(P, c, max_iter);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t assemble_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, int max_defl,
+                               bool vectors, bool mixed, cudaStream_t s) {
+  const int mb = max_items > 0 ? (max_items + 255) / 256 : 1;
+  mu_grouped_kernel<<<mb < 4096 ? mb : 4096, 256, 0, s>>>(P, c);
+  const int ab = max_items > 0 ? (max_items < 65535 ? max_items : 65535) : 1;
+  assemble_grouped_kernel<K><<<ab, kAsmThreads, 0, s>>>(P, c, vectors, mixed);
+  const int db = max_defl > 0 ? (max_defl + 255) / 256 : 1;
+  deflated_grouped_kernel<<<db < 4096 ? db : 4096, 256, 0, s>>>(P, c, vectors, mixed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStream_t s) {
+  class_prefix_kernel<<<1, 32, 0, s>>>(P, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s) {
+  switch (c.K) {
+#define C_(K_) case K_: return counts_grouped_k<K_>(P, c, max_items, s);
+    C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(10) C_(12) C_(14) C_(16)
+#undef C_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
+                                 int num_sms, cudaStream_t s) {
+  switch (c.K) {
+#define R_(K_) case K_: return roots_grouped_k<K_>(P, c, max_items, max_iter, num_sms, s);
+    R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8) R_(10) R_(12) R_(14) R_(16)
+#undef R_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items,
+                                    int max_defl, bool vectors, bool mixed, cudaStream_t s) {
+  switch (c.K) {
+#define A_(K_) case K_: return assemble_grouped_k<K_>(P, c, max_items, max_defl, vectors, mixed, s);
     A_(1) A_(2) A_(3) A_(4) A_(5) A_(6) A_(7) A_(8) A_(10) A_(12) A_(14) A_(16)
 #undef A_
     default: return cudaErrorInvalidValue;

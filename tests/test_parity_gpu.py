@@ -303,3 +303,62 @@ def test_mixed_full_size_sampled(eu, handle_mixed):
     res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu[pos], X[:, pos])
     assert np.max(res) <= RES_TOL * scale
     assert rep["max_residual"] <= RES_TOL * scale and rep["max_orth"] <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Batches: every stage of every update in one grouped launch (per padded rank)
+# ---------------------------------------------------------------------------
+def _batch_problems(count, seed, nmin=64, nmax=700):
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        k = int(rng.integers(1, 17))
+        sg = ["psd", "nsd", "mixed"][t % 3] if k > 1 else "psd"
+        out.append(workloads.general(n, k, seed=seed * 100 + t, sigma=sg, lam_kind=["uniform", "logspec"][t % 2]))
+    return out
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_batch_uneven_sizes_match_solo_and_oracle(eu, handle, handle_mixed, mode):
+    import torch
+
+    h = handle if mode == "fp64" else handle_mixed
+    probs = _batch_problems(24, seed=41 if mode == "fp64" else 42)
+    devs = [dict(Q=dev_colmajor(P["Q"]), lam=dev_vec(P["lam"]), K=dev_colmajor(P["K"]), sigma=P["sigma"],
+                 want=eu.EIG_VALUES | eu.EIG_VECTORS) for P in probs]
+    tickets = eu.eig_update_batch(h, devs)
+    torch.cuda.synchronize()
+    for P, d, t in zip(probs, devs, tickets):
+        assert eu.eig_update_query(h, eu.EIG_Q_STATUS, t) == 0
+        rc, _, mu_s, X_s = _run_update(eu, h, P, want=eu.EIG_VALUES | eu.EIG_VECTORS)
+        assert rc == 0
+        assert np.array_equal(host(d["lam"]), mu_s)       # alone and in the batch: identical
+        assert np.array_equal(host(d["Q"]), X_s)
+        _check_full(P, mu_s, X_s)
+
+
+def test_batch_mixes_values_only_and_invalid(eu, handle):
+    import torch
+
+    probs = _batch_problems(6, seed=7)
+    devs = []
+    for i, P in enumerate(probs):
+        lam = P["lam"].copy()
+        if i == 3:
+            lam = lam[::-1].copy()  # unsorted: rejected on the device, outputs untouched
+        devs.append(dict(Q=dev_colmajor(P["Q"]), lam=dev_vec(lam), K=dev_colmajor(P["K"]), sigma=P["sigma"],
+                         want=eu.EIG_VALUES if i % 2 else eu.EIG_VALUES | eu.EIG_VECTORS))
+    tickets = eu.eig_update_batch(handle, devs)
+    torch.cuda.synchronize()
+    for i, (P, d, t) in enumerate(zip(probs, devs, tickets)):
+        st = eu.eig_update_query(handle, eu.EIG_Q_STATUS, t)
+        if i == 3:
+            assert st == eu.EIG_EINVAL
+            assert np.array_equal(host(d["lam"]), P["lam"][::-1])
+            continue
+        assert st == 0
+        ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], want_vectors=False)
+        assert np.max(np.abs(host(d["lam"]) - ref["mu"])) <= MU_TOL * norm2_A(P["lam"], P["K"])
+        if i % 2:
+            assert np.array_equal(host(d["Q"]), P["Q"])  # values only: Q untouched
