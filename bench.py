@@ -55,6 +55,7 @@ def parse():
                     help="build the Haar Q with numpy on the host instead of a GPU QR")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-update batched measurement")
     return ap.parse_args()
 
 
@@ -273,6 +274,58 @@ def run_mode(eu, h, P, dev, steps, warmup, world):
             "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
 
 
+def run_batched(eu, dev, mode, steps, seed=3000, count=512):
+    """512 independent updates (n log-uniform in [128, 2048], k uniform in 1..8,
+    rank-2-basic recipe) in one eig_update_batch call per step; eigenvectors go
+    to per-update output buffers so that every step repeats identical work."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    t0 = time.perf_counter()
+    probs = workloads.batched(seed=seed, count=count, device=dev)
+    gen_s = time.perf_counter() - t0
+    devs, lam0 = [], []
+    for P in probs:
+        n = P["lam"].shape[0]
+        d = dict(Q=torch.from_numpy(np.asfortranarray(P["Q"])).to(dev),
+                 lam=torch.from_numpy(P["lam"]).to(dev),
+                 K=torch.from_numpy(np.asfortranarray(P["K"])).to(dev), sigma=P["sigma"],
+                 Q_out=torch.empty((n, n), dtype=torch.float64, device=dev).t(),
+                 want=eu.EIG_VALUES | eu.EIG_VECTORS)
+        devs.append(d)
+        lam0.append(d["lam"].clone())
+    h = eu.eig_update_init(dev.index or 0, mode)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for d, l0 in zip(devs, lam0):
+            d["lam"].copy_(l0)
+        tk = eu.eig_update_batch(h, devs, stream=stream)
+        return tk
+
+    for _ in range(2):
+        tk = step()
+    torch.cuda.synchronize()
+    bad = [t for t in tk if eu.eig_update_query(h, eu.EIG_Q_STATUS, t) != 0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    eu.eig_update_destroy(h)
+    pairs = sum(P["lam"].shape[0] for P in probs)
+    return {"value": pairs * steps / (ms / 1000.0), "unit": UNIT, "updates_per_step": count,
+            "eigenpairs_per_step": pairs, "ms_per_step": ms / steps, "steps": steps,
+            "failed_updates": len(bad), "input_generation_s": gen_s,
+            "workload": "512 updates, n log-uniform [128,2048], k uniform 1..8, lam ~ U[-1,1], "
+                        "Q Haar, K ~ N(0,1)/sqrt(n); one eig_update_batch per step (grouped launches)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -351,6 +404,10 @@ def main():
         fp64 = {"value": R64["value"], "unit": UNIT, "ms_per_step": R64["ms"] / len(R64["reps"]),
                 "latency_ms": {"p50": R64["p50"], "p99": R64["p99"]}}
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(eu, dev, main_mode, max(1, min(args.steps, 3)))
+
     # ---- rooflines from the library's own per-stage CUDA events
     peaks, psrc = measured_peaks()
     mean = lambda key: statistics.fmean(r[key] for r in reps)
@@ -392,6 +449,7 @@ def main():
             "stages_ms": stage, "evals_per_root": evals / max(1, n_keep),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
+            "batched": batched,
             "roofline": dominant, "roofline_other": other, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P, args.cpu_sample)

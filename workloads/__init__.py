@@ -30,12 +30,12 @@ def rng_for(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
-def haar(n: int, rng: np.random.Generator, device=None) -> np.ndarray:
+def haar(n: int, rng: np.random.Generator, device=None, min_device_n: int = 1024) -> np.ndarray:
     """Haar-distributed orthogonal matrix: QR of a Gaussian matrix with the
     signs of diag(R) folded into Q (Mezzadri's recipe).  With a CUDA device the
-    QR runs there (input construction only), otherwise numpy."""
+    QR runs there for n >= min_device_n (input construction only), otherwise numpy."""
     G = rng.standard_normal((n, n))
-    if device is not None and n >= 1024:
+    if device is not None and n >= min_device_n:
         import torch
 
         Gt = torch.from_numpy(G).to(device)
@@ -62,11 +62,11 @@ def _sorted_distinct_uniform(n: int, lo: float, hi: float, rng) -> np.ndarray:
     return lam
 
 
-def rank2_basic(seed: int = 0, n: int = 256, k: int = 2, device=None) -> dict:
+def rank2_basic(seed: int = 0, n: int = 256, k: int = 2, device=None, min_device_n: int = 1024) -> dict:
     """Plain PSD rank-k update: lam ~ U[-1,1] sorted, Q Haar, K ~ N(0,1)/sqrt(n)."""
     rng = rng_for(seed)
     lam = _sorted_distinct_uniform(n, -1.0, 1.0, rng)
-    Q = haar(n, rng, device)
+    Q = haar(n, rng, device, min_device_n)
     K = rng.standard_normal((n, k)) / math.sqrt(n)
     return dict(name="rank%d_psd_n%d" % (k, n), Q=Q, lam=lam, K=K,
                 sigma=np.ones(k, dtype=np.int8))
@@ -138,11 +138,11 @@ def batched_sizes(seed: int = 3000, count: int = 512, nmin: int = 128, nmax: int
 
 
 def batched(seed: int = 3000, count: int = 512, nmin: int = 128, nmax: int = 2048,
-            kmax: int = 8) -> list:
+            kmax: int = 8, device=None) -> list:
     """Independent instances, each drawn with the rank2_basic recipe."""
     out = []
     for t, (n, k) in enumerate(batched_sizes(seed, count, nmin, nmax, kmax)):
-        out.append(rank2_basic(seed=seed * 1000 + t, n=n, k=k))
+        out.append(rank2_basic(seed=seed * 1000 + t, n=n, k=k, device=device, min_device_n=256))
     return out
 
 
