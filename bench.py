@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-update batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving measurement")
     return ap.parse_args()
 
 
@@ -326,6 +327,62 @@ def run_batched(eu, dev, mode, steps, seed=3000, count=512):
                         "Q Haar, K ~ N(0,1)/sqrt(n); one eig_update_batch per step (grouped launches)"}
 
 
+def run_serving(eu, dev, mode, residents=12, nmin=1024, nmax=4096, chain=6, load=0.8, seed=4000):
+    """Continuous batching over resident decompositions: saturated throughput with
+    every request queued at once, then a Poisson stream at `load` x that rate;
+    latency = submit to completion seen by the server's poll."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    ns, reqs = workloads.serving_plan(seed=seed, residents=residents, nmin=nmin, nmax=nmax, chain=chain)
+    base = []
+    for r, n in enumerate(ns):
+        P = workloads.rank2_basic(seed=seed * 10 + r, n=n, k=2, device=dev, min_device_n=256)
+        base.append((torch.from_numpy(np.asfortranarray(P["Q"])).to(dev), torch.from_numpy(P["lam"]).to(dev)))
+    payload = [(r, workloads.chained_K(ns[r], k, sd)) for r, k, sd in reqs]
+    pairs = sum(ns[r] for r, _ in payload)
+
+    def session(arrivals):
+        Qs = [q.clone().t().contiguous().t() for q, _ in base]
+        ls = [l.clone() for _, l in base]
+        srv = eu.Server(device=dev.index or 0, mode=mode, slots=2, max_batch=32)
+        ids = [srv.add_resident(Q, l) for Q, l in zip(Qs, ls)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tks = []
+        for j, (r, K) in enumerate(payload):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[j]:
+                    srv.poll(0)
+            tks.append(srv.submit(ids[r], K))
+            srv.poll(0)
+        srv.drain(100)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        infos = [srv.query(t) for t in tks]
+        srv.close()
+        lat = np.array([i["done_ms"] - i["submit_ms"] for i in infos])
+        bad = sum(1 for i in infos if i["status"] != 0)
+        return wall, lat, bad, float(np.mean([i["batch_size"] for i in infos]))
+
+    session(None)  # warm-up
+    wall_sat, lat_sat, bad_sat, bs_sat = session(None)
+    rate = load * len(payload) / wall_sat
+    arr = workloads.poisson_arrivals(rate, len(payload), seed + 1)
+    wall, lat, bad, bs = session(arr)
+    return {"value": pairs / wall, "unit": UNIT, "requests": len(payload), "residents": residents,
+            "chain": chain, "offered_rate_req_s": rate, "achieved_req_s": len(payload) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "saturated": {"value": pairs / wall_sat, "req_s": len(payload) / wall_sat,
+                          "mean_batch": bs_sat},
+            "mean_batch": bs, "failed": bad + bad_sat,
+            "workload": "%d residents, n log-uniform [%d,%d], %d chained rank-k updates each (k uniform 2..8, "
+                        "K ~ N(0,1)/sqrt(n)), Poisson arrivals at %.1f x saturated rate" % (
+                            residents, nmin, nmax, chain, load)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -407,6 +464,9 @@ def main():
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(eu, dev, main_mode, max(1, min(args.steps, 3)))
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(eu, dev, main_mode)
 
     # ---- rooflines from the library's own per-stage CUDA events
     peaks, psrc = measured_peaks()
@@ -450,6 +510,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
             "batched": batched,
+            "serving": serving,
             "roofline": dominant, "roofline_other": other, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P, args.cpu_sample)

@@ -218,6 +218,54 @@ int eig_secular_values_static(int64_t n, int32_t k, const double* lambda, const 
                               const int8_t* sigma, double* mu, int32_t* iters, int32_t max_iter,
                               void* stream);
 
+/* ---- serving: resident decompositions, continuous batching -----------------
+ * A server keeps decompositions (Q, lambda) resident on the device and applies
+ * rank-k update requests to them in order (chained updates).  Requests carry
+ * K on the host; eig_server_poll reaps finished batches and admits pending
+ * requests into new batches whenever a batch slot (stream + workspace of
+ * hbm_budget / slots bytes) is free: at most one request per resident per
+ * batch (so a chain stays ordered), as many as fit the slot's workspace.
+ * Batches on different slots overlap on the device.  Every batch is one
+ * grouped eig_update_batch-style launch sequence; each result is identical to
+ * the same update applied alone.  Not thread-safe: one host thread drives a
+ * server. */
+typedef struct eig_srv* eig_server;
+
+typedef struct {
+  int32_t device;
+  uint32_t mode;        /* EIG_FP64 or EIG_MIXED */
+  uint64_t hbm_budget;  /* workspace bytes over all slots; 0 = 8 GiB */
+  int32_t slots;        /* batches in flight; 0 = 2 */
+  int32_t max_batch;    /* requests per batch; 0 = 64 */
+} eig_server_params;
+
+typedef struct {
+  int32_t status;       /* EIG_EBUSY while queued or running */
+  int32_t resident;
+  int32_t k;
+  int32_t batch_size;   /* requests in the batch that carried it */
+  double submit_ms;     /* host clock, ms since the server was created */
+  double launch_ms;
+  double done_ms;       /* when eig_server_poll saw the batch finish */
+} eig_request_info;
+
+int eig_server_create(const eig_server_params* params, eig_server* out);
+int eig_server_destroy(eig_server srv);
+/* Register a resident decomposition: device Q (n x n, column-major) and lambda
+   (n, ascending), owned by the caller and updated in place by every request. */
+int eig_server_add_resident(eig_server srv, int64_t n, double* Q, double* lambda, int32_t* id);
+/* Queue a rank-k update of resident `id`: K (host, n x k column-major) and
+   sigma (host, NULL = all +1) are copied at submit.  Returns a ticket. */
+int eig_server_submit(eig_server srv, int32_t id, int32_t k, const double* K, const int8_t* sigma,
+                      uint64_t* ticket);
+/* Reap finished batches and launch new ones; waits up to wait_us for one
+   batch to finish when nothing can be launched.  Returns the number of
+   requests completed by this call (>= 0) or an EIG_E* code. */
+int eig_server_poll(eig_server srv, int32_t wait_us);
+int eig_server_query(eig_server srv, uint64_t ticket, eig_request_info* out);
+/* Requests still queued or running. */
+int eig_server_pending(eig_server srv);
+
 /* Sec. 2.2 Steps 1-2: write K = [(e_j + a)/sqrt(2), (e_j - a)/sqrt(2)] (device
    n x 2) and sigma = {+1, -1} (host) so that K Sigma K^T = e_j a^T + a e_j^T.
    a is device n.  Stream-ordered. */

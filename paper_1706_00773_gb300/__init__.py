@@ -23,6 +23,8 @@ __all__ = [
     "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
     "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
+    "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
+    "eig_server_poll", "eig_server_query", "eig_server_pending", "Server",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
@@ -74,6 +76,20 @@ class eig_report(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class eig_server_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("mode", ctypes.c_uint32), ("hbm_budget", ctypes.c_uint64),
+                ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+
+
+class eig_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("resident", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("submit_ms", ctypes.c_double), ("launch_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class eig_count_args(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("npts", ctypes.c_int32),
                 ("lambda_", ctypes.c_void_p), ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
@@ -101,6 +117,16 @@ def lib() -> ctypes.CDLL:
         L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
         L.eig_make_rank2.argtypes = [i64, i64, vp, vp, vp, vp]
         L.eig_secular_values_static.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp]
+        L.eig_server_create.argtypes = [ctypes.POINTER(eig_server_params), ctypes.POINTER(vp)]
+        L.eig_server_destroy.argtypes = [vp]
+        L.eig_server_add_resident.argtypes = [vp, i64, vp, vp, ctypes.POINTER(i32)]
+        L.eig_server_submit.argtypes = [vp, i32, i32, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.eig_server_poll.argtypes = [vp, i32]
+        L.eig_server_query.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(eig_request_info)]
+        L.eig_server_pending.argtypes = [vp]
+        for f in ("eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
+                  "eig_server_poll", "eig_server_query", "eig_server_pending"):
+            getattr(L, f).restype = ctypes.c_int
         L.eig_version.restype = ctypes.c_char_p
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
                   "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
@@ -312,6 +338,100 @@ class Updater:
         if self.h:
             eig_update_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Serving (continuous batching over resident decompositions)
+# ---------------------------------------------------------------------------
+def eig_server_create(device: int = 0, mode: int = EIG_MIXED, hbm_budget: int = 0, slots: int = 0,
+                      max_batch: int = 0):
+    p = eig_server_params(device, mode, hbm_budget, slots, max_batch)
+    s = ctypes.c_void_p()
+    _check(lib().eig_server_create(ctypes.byref(p), ctypes.byref(s)), "eig_server_create")
+    return s
+
+
+def eig_server_destroy(srv) -> None:
+    _check(lib().eig_server_destroy(srv), "eig_server_destroy")
+
+
+def eig_server_add_resident(srv, Q, lam) -> int:
+    out = ctypes.c_int32()
+    _check(lib().eig_server_add_resident(srv, int(lam.shape[0]), _ptr(Q, "Q", True), _ptr(lam, "lambda"),
+                                         ctypes.byref(out)), "eig_server_add_resident")
+    return int(out.value)
+
+
+def eig_server_submit(srv, resident: int, K_host, sigma=None) -> int:
+    """K_host: numpy (n, k) float64 (any layout; copied column-major)."""
+    import numpy as np
+
+    K = np.asfortranarray(np.asarray(K_host, dtype=np.float64))
+    if K.ndim == 1:
+        K = K.reshape(-1, 1, order="F")
+    k = int(K.shape[1])
+    sbuf, sp = _sigma_buf(sigma, k)
+    t = ctypes.c_uint64()
+    _check(lib().eig_server_submit(srv, int(resident), k, K.ctypes.data_as(ctypes.c_void_p), sp, ctypes.byref(t)),
+           "eig_server_submit")
+    del sbuf
+    return int(t.value)
+
+
+def eig_server_poll(srv, wait_us: int = 0) -> int:
+    rc = lib().eig_server_poll(srv, int(wait_us))
+    if rc < 0:
+        raise EigError(rc, "eig_server_poll")
+    return rc
+
+
+def eig_server_query(srv, ticket: int) -> dict:
+    info = eig_request_info()
+    lib().eig_server_query(srv, ctypes.c_uint64(ticket), ctypes.byref(info))
+    return info.as_dict()
+
+
+def eig_server_pending(srv) -> int:
+    return int(lib().eig_server_pending(srv))
+
+
+class Server:
+    """``Server(mode=...)``: add_resident(Q, lam) -> id, submit(id, K_host, sigma) -> ticket,
+    poll(), drain(), query(ticket)."""
+
+    def __init__(self, device: int = 0, mode: int = EIG_MIXED, hbm_budget: int = 0, slots: int = 0,
+                 max_batch: int = 0):
+        self.s = eig_server_create(device, mode, hbm_budget, slots, max_batch)
+
+    def add_resident(self, Q, lam) -> int:
+        return eig_server_add_resident(self.s, Q, lam)
+
+    def submit(self, resident: int, K_host, sigma=None) -> int:
+        return eig_server_submit(self.s, resident, K_host, sigma)
+
+    def poll(self, wait_us: int = 0) -> int:
+        return eig_server_poll(self.s, wait_us)
+
+    def pending(self) -> int:
+        return eig_server_pending(self.s)
+
+    def drain(self, wait_us: int = 200) -> None:
+        while self.pending() > 0:
+            self.poll(wait_us)
+
+    def query(self, ticket: int) -> dict:
+        return eig_server_query(self.s, ticket)
+
+    def close(self):
+        if self.s:
+            eig_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -6,7 +6,10 @@
 #include <cstdint>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
+#include <deque>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <vector>
 
@@ -774,9 +777,9 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       if (!P || !out || out_bytes < sizeof(uint64_t) || P->n < 1 || P->k < 1 || P->k > EIG_MAX_K)
         return EIG_EINVAL;
       const bool vectors = (P->want & EIG_VECTORS) != 0;
-      *static_cast<uint64_t*>(out) = plan(nullptr, P->n, P->k, vectors, P->Q_out == nullptr,
-                                          (P->want & EIG_REPORT) && vectors, h->mode == EIG_MIXED)
-                                         .bytes;
+      std::vector<TableItem> one{{P, 0, P->k, (P->want & EIG_REPORT) && vectors}};
+      *static_cast<uint64_t*>(out) =
+          layout_table(h, one, nullptr, vectors, h->mode == EIG_MIXED, nullptr).bytes;
       return EIG_OK;
     }
     case EIG_Q_COUNT: {
@@ -872,6 +875,316 @@ int eig_make_rank2(int64_t n, int64_t j, const double* a, double* K, int8_t* sig
   sigma[1] = -1;
   CK(launch_make_rank2(n, j, a, K, static_cast<cudaStream_t>(stream)));
   return EIG_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Serving: resident decompositions, chained requests, continuous batching.
+// ===========================================================================
+struct SrvRequest {
+  int resident = 0;
+  int k = 0;
+  std::vector<double> K;  // host copy, n x k column-major
+  std::vector<int8_t> sigma;
+  unsigned long long negmask = 0;
+  int kplus = 0;
+  int status = EIG_EBUSY;
+  int batch_size = 0;
+  double submit_ms = 0, launch_ms = -1, done_ms = -1;
+};
+
+struct SrvResident {
+  int64_t n = 0;
+  double* Q = nullptr;
+  double* lambda = nullptr;
+  bool busy = false;
+};
+
+struct SrvSlot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* kstage = nullptr;  // pinned staging for the batch's K payloads
+  size_t kstage_bytes = 0;
+  DevStatus* st_host = nullptr;  // pinned, max_batch entries
+  bool busy = false;
+  std::vector<uint64_t> reqs;
+  std::vector<eig_problem> probs;
+};
+
+struct eig_srv {
+  eig_ctx* h = nullptr;
+  int max_batch = 64;
+  bool mixed = false;
+  std::vector<SrvSlot> slots;
+  std::vector<SrvResident> residents;
+  std::deque<uint64_t> pending;
+  std::vector<SrvRequest> reqs;
+  int inflight = 0;
+  std::chrono::steady_clock::time_point t0;
+  double now_ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace {
+
+size_t srv_request_bytes(eig_srv* S, const SrvRequest& r) {
+  const SrvResident& res = S->residents[r.resident];
+  eig_problem P{};
+  P.n = res.n;
+  P.k = r.k;
+  P.want = EIG_VALUES | EIG_VECTORS;
+  std::vector<TableItem> one{{&P, 0, r.k, false}};
+  return layout_table(S->h, one, nullptr, true, S->mixed, nullptr).bytes + 4096 +
+         align_up(sizeof(double) * (size_t)res.n * r.k, 256);
+}
+
+// Reap every finished batch; returns requests completed.
+int srv_reap(eig_srv* S) {
+  int done = 0;
+  for (SrvSlot& sl : S->slots) {
+    if (!sl.busy) continue;
+    const cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) {
+      cudaGetLastError();
+      continue;
+    }
+    const double t = S->now_ms();
+    for (size_t j = 0; j < sl.reqs.size(); ++j) {
+      SrvRequest& r = S->reqs[sl.reqs[j] - 1];
+      r.status = (q == cudaSuccess) ? status_of(sl.st_host[j]) : EIG_ECUDA;
+      r.done_ms = t;
+      S->residents[r.resident].busy = false;
+      ++done;
+    }
+    if (q != cudaSuccess) cudaGetLastError();
+    S->inflight -= (int)sl.reqs.size();
+    sl.reqs.clear();
+    sl.busy = false;
+  }
+  return done;
+}
+
+// Admit pending requests into a batch on a free slot and launch it.
+int srv_launch(eig_srv* S, SrvSlot& sl) {
+  std::vector<uint64_t> pick;
+  std::vector<char> taken(S->residents.size(), 0);
+  size_t bytes = 0, kbytes = 0;
+  for (auto it = S->pending.begin(); it != S->pending.end() && (int)pick.size() < S->max_batch;) {
+    SrvRequest& r = S->reqs[*it - 1];
+    if (S->residents[r.resident].busy || taken[r.resident]) {
+      ++it;
+      continue;
+    }
+    const size_t need = srv_request_bytes(S, r);
+    if (need > sl.ws_bytes) {  // can never fit this slot: reject
+      r.status = EIG_ENOMEM;
+      r.done_ms = S->now_ms();
+      it = S->pending.erase(it);
+      continue;
+    }
+    if (bytes + need > sl.ws_bytes) break;  // admission by free workspace
+    bytes += need;
+    kbytes += align_up(sizeof(double) * (size_t)S->residents[r.resident].n * r.k, 256);
+    taken[r.resident] = 1;
+    pick.push_back(*it);
+    it = S->pending.erase(it);
+  }
+  if (pick.empty()) return 0;
+  if (kbytes > sl.kstage_bytes) {
+    if (sl.kstage) cudaFreeHost(sl.kstage);
+    sl.kstage = nullptr;
+    sl.kstage_bytes = 0;
+    if (cudaMallocHost(&sl.kstage, kbytes) != cudaSuccess) {
+      cudaGetLastError();
+      for (uint64_t t : pick) S->pending.push_front(t);
+      return EIG_ENOMEM;
+    }
+    sl.kstage_bytes = kbytes;
+  }
+  // K payloads: pinned staging -> the head of the slot workspace.
+  sl.probs.assign(pick.size(), eig_problem{});
+  std::vector<TableItem> items;
+  size_t koff = 0;
+  for (size_t j = 0; j < pick.size(); ++j) {
+    SrvRequest& r = S->reqs[pick[j] - 1];
+    SrvResident& res = S->residents[r.resident];
+    const size_t kb = sizeof(double) * (size_t)res.n * r.k;
+    std::memcpy(reinterpret_cast<char*>(sl.kstage) + koff, r.K.data(), kb);
+    eig_problem& P = sl.probs[j];
+    P.n = res.n;
+    P.k = r.k;
+    P.Q = res.Q;
+    P.lambda = res.lambda;
+    P.K = reinterpret_cast<const double*>(sl.ws + koff);
+    P.sigma = r.sigma.empty() ? nullptr : r.sigma.data();
+    P.Q_out = nullptr;
+    P.want = EIG_VALUES | EIG_VECTORS;
+    items.push_back({&P, r.negmask, r.kplus, false});
+    koff += align_up(kb, 256);
+  }
+  CK(cudaMemcpyAsync(sl.ws, sl.kstage, koff, cudaMemcpyHostToDevice, sl.stream));
+  std::vector<char> img;
+  Table T = layout_table(S->h, items, sl.ws + koff, true, S->mixed, &img);
+  if (T.bytes == 0) return EIG_ECUDA;
+  int nl = 0;
+  int rc = enqueue_table(S->h, T, (int)items.size(), true, S->mixed, false, sl.stream, nullptr, &nl, img,
+                         nullptr, 0);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(sl.st_host, T.d_st, sizeof(DevStatus) * items.size(), cudaMemcpyDeviceToHost,
+                     sl.stream));
+  CK(cudaEventRecord(sl.done, sl.stream));
+  const double t = S->now_ms();
+  for (uint64_t tk : pick) {
+    SrvRequest& r = S->reqs[tk - 1];
+    r.launch_ms = t;
+    r.batch_size = (int)pick.size();
+    S->residents[r.resident].busy = true;
+  }
+  sl.reqs = pick;
+  sl.busy = true;
+  S->inflight += (int)pick.size();
+  return (int)pick.size();
+}
+
+}  // namespace
+
+extern "C" {
+
+int eig_server_create(const eig_server_params* params, eig_server* out) {
+  if (!out) return EIG_EINVAL;
+  *out = nullptr;
+  eig_server_params p{};
+  if (params) p = *params;
+  const int slots = p.slots > 0 ? p.slots : 2;
+  const int max_batch = p.max_batch > 0 ? p.max_batch : 64;
+  const uint64_t budget = p.hbm_budget ? p.hbm_budget : (uint64_t)8 << 30;
+  if (slots > 16 || max_batch > 4096) return EIG_EINVAL;
+  eig_init_params ip{};
+  ip.device = p.device;
+  ip.mode = p.mode;
+  eig_handle h = nullptr;
+  int rc = eig_update_init(&ip, &h);
+  if (rc) return rc;
+  eig_srv* S = new (std::nothrow) eig_srv();
+  if (!S) {
+    eig_update_destroy(h);
+    return EIG_ENOMEM;
+  }
+  S->h = h;
+  S->max_batch = max_batch;
+  S->mixed = p.mode == EIG_MIXED;
+  S->t0 = std::chrono::steady_clock::now();
+  S->slots.resize(slots);
+  DeviceGuard g(h->device);
+  for (SrvSlot& sl : S->slots) {
+    sl.ws_bytes = align_up(budget / slots, 256);
+    void* w = nullptr;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&w, sl.ws_bytes) != cudaSuccess ||
+        cudaMallocHost(&sl.st_host, sizeof(DevStatus) * max_batch) != cudaSuccess) {
+      cudaGetLastError();
+      if (w) sl.ws = static_cast<char*>(w);
+      eig_server_destroy(S);
+      return EIG_ENOMEM;
+    }
+    sl.ws = static_cast<char*>(w);
+  }
+  *out = S;
+  return EIG_OK;
+}
+
+int eig_server_destroy(eig_server S) {
+  if (!S) return EIG_OK;
+  {
+    DeviceGuard g(S->h->device);
+    for (SrvSlot& sl : S->slots) {
+      if (sl.stream) cudaStreamSynchronize(sl.stream);
+      if (sl.ws) cudaFree(sl.ws);
+      if (sl.kstage) cudaFreeHost(sl.kstage);
+      if (sl.st_host) cudaFreeHost(sl.st_host);
+      if (sl.done) cudaEventDestroy(sl.done);
+      if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    cudaGetLastError();
+  }
+  eig_update_destroy(S->h);
+  delete S;
+  return EIG_OK;
+}
+
+int eig_server_add_resident(eig_server S, int64_t n, double* Q, double* lambda, int32_t* id) {
+  if (!S || n < 1 || n > (int64_t)0x3fffffff || !Q || !lambda || !id) return EIG_EINVAL;
+  SrvResident r;
+  r.n = n;
+  r.Q = Q;
+  r.lambda = lambda;
+  S->residents.push_back(r);
+  *id = (int32_t)S->residents.size() - 1;
+  return EIG_OK;
+}
+
+int eig_server_submit(eig_server S, int32_t id, int32_t k, const double* K, const int8_t* sigma,
+                      uint64_t* ticket) {
+  if (!S || id < 0 || id >= (int32_t)S->residents.size() || k < 1 || k > EIG_MAX_K || !K || !ticket)
+    return EIG_EINVAL;
+  SrvRequest r;
+  if (!sigma_info(sigma, k, &r.negmask, &r.kplus)) return EIG_EINVAL;
+  r.resident = id;
+  r.k = k;
+  const int64_t n = S->residents[id].n;
+  r.K.assign(K, K + (size_t)n * k);
+  if (sigma) r.sigma.assign(sigma, sigma + k);
+  r.submit_ms = S->now_ms();
+  S->reqs.push_back(std::move(r));
+  *ticket = (uint64_t)S->reqs.size();
+  S->pending.push_back(*ticket);
+  return EIG_OK;
+}
+
+int eig_server_poll(eig_server S, int32_t wait_us) {
+  if (!S) return EIG_EINVAL;
+  DeviceGuard g(S->h->device);
+  if (!g.ok) return EIG_ECUDA;
+  int done = srv_reap(S);
+  bool launched = false;
+  for (SrvSlot& sl : S->slots) {
+    if (sl.busy || S->pending.empty()) continue;
+    const int rc = srv_launch(S, sl);
+    if (rc < 0) return rc;
+    launched = launched || rc > 0;
+  }
+  if (!launched && done == 0 && S->inflight > 0 && wait_us > 0) {
+    const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(wait_us);
+    while (std::chrono::steady_clock::now() < until) {
+      done = srv_reap(S);
+      if (done > 0) break;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+  return done;
+}
+
+int eig_server_query(eig_server S, uint64_t ticket, eig_request_info* out) {
+  if (!S || !out || ticket < 1 || ticket > S->reqs.size()) return EIG_EINVAL;
+  const SrvRequest& r = S->reqs[ticket - 1];
+  out->status = r.status;
+  out->resident = r.resident;
+  out->k = r.k;
+  out->batch_size = r.batch_size;
+  out->submit_ms = r.submit_ms;
+  out->launch_ms = r.launch_ms;
+  out->done_ms = r.done_ms;
+  return r.status;
+}
+
+int eig_server_pending(eig_server S) {
+  if (!S) return EIG_EINVAL;
+  return (int)S->pending.size() + S->inflight;
 }
 
 }  // extern "C"

@@ -454,6 +454,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, slow = 0, ia = -1, ib = -1;
   bool has_a = false, has_b = false, first = false, notconv = false;
   double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
+  bool last_model = false;  // the current point came from a two-pole model step
   if (e == 0) {
     int lo = 0, hi = n;  // p = #{q : pole_cnt[q] <= m}
     while (lo < hi) {
@@ -583,6 +584,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
       const int count = below + __popc(posmask) - posD - sub.kplus;
       ++it;
+      const double wprev = th - tl;
       if (count <= m) {
         tl = tau;
         c_lo = count;
@@ -590,6 +592,9 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
         th = tau;
         c_hi = count;
       }
+      // A model step that did not halve the bracket is not trusted again (it
+      // can keep aiming at a neighbouring root): bisect instead.
+      const bool stalled = last_model && (th - tl) > 0.5 * wprev;
       if (first) {
         first = false;
         if (count <= m) {  // root above the midpoint: measure it from pole b
@@ -639,7 +644,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const int inb = c_hi - c_lo;  // roots in the bracket
       const int r_in = m - c_lo;    // our root's rank among them
       double model = NAN;
-      if (ncand > 0) {
+      if (ncand > 0 && !stalled) {
         if (inb == ncand) model = (r_in >= 1 && ncand == 2) ? cand1 : cand0;
         else if (inb == 1) model = cand0;
       }
@@ -663,6 +668,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           if (slow >= 3 && !conv) {
             newton = false;
             slow = 0;
+            tn = NAN;  // fall through to bisection
           }
         } else if (isfinite(model)) {
           tn = model;
@@ -672,6 +678,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       } else {
         tn = isfinite(model) ? model : NAN;
       }
+      last_model = !newton && !conv && isfinite(model) && tn == model;
       if (!conv && !newton && !(tn > tl && tn < th)) {
         tn = tl + 0.5 * (th - tl);
         if (tl > 0.0 && th > 64.0 * tl) tn = sqrt(tl) * sqrt(th);
