@@ -7,7 +7,9 @@ only module both sides share is ``workloads`` (seeded input generators).
 
 Plain and slow on purpose.  The C part (``orc.c``) holds the Jacobi
 eigensolver, the root count, the bisection root finder and the eq. (10)
-vectors.  This module composes them with numpy library primitives (matmul).
+vectors.  This module composes them with numpy library primitives (matmul),
+and adds the rank-2 location vector (Algorithms 1a-1c, with the residues of
+eq. (3)) and the exact-rational Sturm chain of Sec. 2.2 for tiny problems.
 Each function names the passage of the paper it follows.  The paper prints no
 worked example, so every pin is a closed form, an invariant, a special case or
 a library routine (``tests/test_oracle_pins.py``).
@@ -330,3 +332,204 @@ def orthogonality(X):
     X = np.asarray(X, dtype=np.float64)
     G = X.T @ X
     return float(np.max(np.abs(G - np.eye(G.shape[0]))))
+
+
+# ---------------------------------------------------------------------------
+# Location sub-problem, rank 2 (Sec. 2.2, Algorithms 1a-1c)
+# ---------------------------------------------------------------------------
+def residues(lam, U, sigma=None):
+    """alpha_i of eq. (3), f(x) = 1 + sum_i alpha_i/(lam_i - x), for
+    f(x) = det(I - Sigma U^T (xI - Lam)^{-1} U): with B_i = I + Sigma U^T D_i U,
+    D_i = diag(1/(lam_j - lam_i)) (j != i), alpha_i = u_i^T adj(B_i) Sigma u_i
+    (eq. (2) with its sign corrected).  Distinct lam required."""
+    lam = np.asarray(lam, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64).reshape(lam.shape[0], -1)
+    n, k = U.shape
+    S = np.diag(_sig(sigma, k).astype(np.float64))
+    out = np.zeros(n)
+    for i in range(n):
+        d = np.zeros(n)
+        m = np.arange(n) != i
+        d[m] = 1.0 / (lam[m] - lam[i])
+        B = np.eye(k) + S @ U.T @ (U * d[:, None])
+        if k == 1:
+            adj = np.ones((1, 1))
+        elif k == 2:
+            adj = np.array([[B[1, 1], -B[0, 1]], [-B[1, 0], B[0, 0]]])
+        else:
+            adj = np.linalg.det(B) * np.linalg.inv(B)
+        out[i] = U[i] @ adj @ S @ U[i]
+    return out
+
+
+def location_vector(lam, U, sigma, printed_1c=False):
+    """Algorithms 1a-1c for a rank-2 update: L[0] roots below lam_1, L[i]
+    roots in (lam_i, lam_{i+1}), L[n] roots above lam_n (0-based L of length
+    n+1).  1a (both sigma > 0) scans up from the left; 1b (both < 0) is its
+    mirror from the right (the bound on the roots placed so far is the
+    mirrored one of 1a); 1c (opposite signs) starts from the sign of the
+    first residue and scans up.  Where the listings read mu_{n+1} or mu_0
+    (undefined), the last interval takes the roots not placed yet.
+
+    With opposite signs every new root lies within one pole of its old
+    eigenvalue, so at most i+1 roots lie below lam_{i+1}: the 0-or-2 choice
+    of 1c compares M+2 with i+1.  printed_1c=True keeps the bound of 1a
+    (M+2 > i) as the listing of 1c prints it, which misplaces roots."""
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[0]
+    s = _sig(sigma, 2)
+    a = residues(lam, U, s)
+    L = np.zeros(n + 1, dtype=np.int64)
+    if s[0] > 0 and s[1] > 0:
+        M = 0
+        for i in range(1, n):  # interval (lam_i, lam_{i+1}) in 1-based terms -> L[i]
+            if a[i - 1] * a[i] > 0:
+                L[i] = 1
+                M += 1
+            elif M + 2 > i:
+                L[i] = 0
+            else:
+                L[i] = 2
+                M += 2
+        L[n] = n - M
+    elif s[0] < 0 and s[1] < 0:
+        M = 0
+        for i in range(1, n):  # mirror: interval (lam_{n-i}, lam_{n-i+1}) -> L[n-i]
+            j = n - i
+            if a[j - 1] * a[j] > 0:
+                L[j] = 1
+                M += 1
+            elif M + 2 > i:
+                L[j] = 0
+            else:
+                L[j] = 2
+                M += 2
+        L[0] = n - M
+    else:
+        if a[0] > 0:
+            M, L[0] = 0, 0
+        else:
+            M, L[0] = 1, 1
+        bound = 0 if printed_1c else 1
+        for i in range(1, n):
+            if a[i - 1] * a[i] > 0:
+                L[i] = 1
+                M += 1
+            elif M + 2 > i + bound:
+                L[i] = 0
+            else:
+                L[i] = 2
+                M += 2
+        L[n] = n - M
+    return L
+
+
+# ---------------------------------------------------------------------------
+# The Sturm chain of Sec. 2.2 in exact rational arithmetic (tiny n only)
+# ---------------------------------------------------------------------------
+def _frac_det(M):
+    from fractions import Fraction
+
+    A = [[Fraction(v) for v in row] for row in M]
+    n = len(A)
+    det = Fraction(1)
+    for c in range(n):
+        p = next((r for r in range(c, n) if A[r][c] != 0), None)
+        if p is None:
+            return Fraction(0)
+        if p != c:
+            A[c], A[p] = A[p], A[c]
+            det = -det
+        det *= A[c][c]
+        for r in range(c + 1, n):
+            f = A[r][c] / A[c][c]
+            for j in range(c, n):
+                A[r][j] -= f * A[c][j]
+    return det
+
+
+def _poly_from_values(xs, ys):
+    """Exact interpolation: coefficients (lowest degree first) through (xs, ys)."""
+    from fractions import Fraction
+
+    n = len(xs)
+    coef = [Fraction(0)] * n
+    for i in range(n):
+        basis = [Fraction(1)]
+        den = Fraction(1)
+        for j in range(n):
+            if j == i:
+                continue
+            basis = [Fraction(0)] + basis
+            for t in range(len(basis) - 1):
+                basis[t] -= xs[j] * basis[t + 1]
+            den *= xs[i] - xs[j]
+        for t in range(n):
+            coef[t] += ys[i] * basis[t] / den
+    return coef
+
+
+def _trim(p):
+    while len(p) > 1 and p[-1] == 0:
+        p = p[:-1]
+    return p
+
+
+def _polyrem(a, b):
+    from fractions import Fraction
+
+    a = list(a)
+    b = _trim(list(b))
+    while len(_trim(a)) >= len(b) and any(v != 0 for v in a):
+        a = _trim(a)
+        if len(a) < len(b):
+            break
+        f = a[-1] / b[-1]
+        sh = len(a) - len(b)
+        for t in range(len(b)):
+            a[sh + t] -= f * b[t]
+        a = a[:-1] if a[-1] == 0 else a
+    return _trim(a) if a else [Fraction(0)]
+
+
+def sturm_chain(lam, U, sigma=None):
+    """p_0 = prod(x - lam_i) f_0(x) = det(xI - A') (the numerator of the
+    secular function, eq. (5)), p_1 = p_0', p_m = -rem(p_{m-2}, p_{m-1}):
+    the chain the secular long division of Sec. 2.2 builds, here in exact
+    rationals from the exact float inputs."""
+    from fractions import Fraction
+
+    lam = np.asarray(lam, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64).reshape(lam.shape[0], -1)
+    n, k = U.shape
+    S = _sig(sigma, k)
+    Uf = [[Fraction(float(U[i, c])) for c in range(k)] for i in range(n)]
+    A = [[(Fraction(float(lam[i])) if i == j else Fraction(0)) +
+          sum(Uf[i][c] * Uf[j][c] * int(S[c]) for c in range(k)) for j in range(n)] for i in range(n)]
+    xs = [Fraction(t) for t in range(n + 1)]
+    ys = [_frac_det([[(xs[t] if i == j else 0) - A[i][j] for j in range(n)] for i in range(n)]) for t in range(n + 1)]
+    p0 = _poly_from_values(xs, ys)
+    p1 = [p0[t] * t for t in range(1, len(p0))]
+    chain = [_trim(p0), _trim(p1)]
+    while len(chain[-1]) > 1 or chain[-1][0] != 0:
+        r = _polyrem(chain[-2], chain[-1])
+        if all(v == 0 for v in r):
+            break
+        chain.append([-v for v in r])
+        if len(chain[-1]) == 1:
+            break
+    return chain
+
+
+def sturm_count(chain, x) -> int:
+    """Number of distinct roots of p_0 below x: V(-inf) - V(x), V = sign changes."""
+    from fractions import Fraction
+
+    def sign_changes(vals):
+        s = [v for v in vals if v != 0]
+        return sum(1 for a, b in zip(s, s[1:]) if (a > 0) != (b > 0))
+
+    X = Fraction(float(x))
+    at_x = [sum(c * X ** t for t, c in enumerate(p)) for p in chain]
+    at_minf = [c[-1] * (1 if (len(c) - 1) % 2 == 0 else -1) for c in chain]
+    return sign_changes(at_minf) - sign_changes(at_x)
