@@ -271,6 +271,23 @@ int eig_server_pending(eig_server srv);
    a is device n.  Stream-ordered. */
 int eig_make_rank2(int64_t n, int64_t j, const double* a, double* K, int8_t* sigma, void* stream);
 
+/* Sec. 2.2, eq. (3) and Algorithms 1a-1c: the location vector of a rank-2
+   update diag(lambda) + U Sigma U^T.  lambda (device n, strictly ascending:
+   deflated, distinct poles), U (device n x 2, column-major), sigma (host 2
+   entries of +1/-1; NULL = {+1, +1}).  Writes alpha (device n) = the residues
+   of f(x) = 1 + sum_i alpha_i / (lambda_i - x), and L (device int32 n+1):
+   L[0] roots below lambda_0, L[i] roots in (lambda_{i-1}, lambda_i), L[n]
+   roots above lambda_{n-1}.  Both sigma > 0 scans from the left (1a), both
+   < 0 from the right (1b), opposite signs from the left after placing 0 or 1
+   root below lambda_0 by the sign of alpha_0 (1c, with the bound of at most
+   i+1 roots below lambda_i).  The roots are counted from residue signs only,
+   so a residue that rounds to the wrong sign (a pole that nearly deflates)
+   misplaces roots: the inertia count of eig_update_query(EIG_Q_COUNT) has no
+   such limit.  O(n^2) work.  Stream-ordered; the caller owns every buffer.
+   EIG_EINVAL for n < 2, NULL buffers or sigma entries other than +1/-1. */
+int eig_location_rank2(int64_t n, const double* lambda, const double* U, const int8_t* sigma,
+                       double* alpha, int32_t* L, void* stream);
+
 /* Library version string (static storage). */
 const char* eig_version(void);
 

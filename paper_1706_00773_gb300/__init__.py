@@ -24,7 +24,7 @@ __all__ = [
     "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
-    "eig_server_poll", "eig_server_query", "eig_server_pending", "Server",
+    "eig_server_poll", "eig_server_query", "eig_server_pending", "Server", "eig_location_rank2",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         L.eig_project.argtypes = [vp, i64, i32, vp, vp, vp, vp]
         L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
         L.eig_make_rank2.argtypes = [i64, i64, vp, vp, vp, vp]
+        L.eig_location_rank2.argtypes = [i64, vp, vp, vp, vp, vp, vp]
         L.eig_secular_values_static.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp]
         L.eig_server_create.argtypes = [ctypes.POINTER(eig_server_params), ctypes.POINTER(vp)]
         L.eig_server_destroy.argtypes = [vp]
@@ -130,7 +131,7 @@ def lib() -> ctypes.CDLL:
         L.eig_version.restype = ctypes.c_char_p
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
                   "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
-                  "eig_secular_values_static"):
+                  "eig_secular_values_static", "eig_location_rank2"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -323,6 +324,22 @@ def eig_make_rank2(n: int, j: int, a, K, stream=None):
     _check(lib().eig_make_rank2(n, j, _ptr(a, "a"), _ptr(K, "K", True), ctypes.cast(sig, ctypes.c_void_p),
                                 _stream(stream)), "eig_make_rank2")
     return [int(sig[0]), int(sig[1])]
+
+
+def eig_location_rank2(lam, U, sigma, alpha, L, stream=None) -> None:
+    """Residues (device n) and location vector (device int32 n+1) of a rank-2
+    update diag(lam) + U Sigma U^T (Algorithms 1a-1c)."""
+    import torch
+
+    n = int(lam.shape[0])
+    if int(U.shape[1]) != 2:
+        raise ValueError("the location vector is defined for rank 2")
+    if L.dtype != torch.int32 or not L.is_cuda or int(L.numel()) < n + 1:
+        raise TypeError("L must be a CUDA int32 tensor of n+1 entries")
+    sbuf, sp = _sigma_buf(sigma, 2)
+    _check(lib().eig_location_rank2(n, _ptr(lam, "lambda"), _ptr(U, "U", True), sp, _ptr(alpha, "alpha"),
+                                    ctypes.c_void_p(L.data_ptr()), _stream(stream)), "eig_location_rank2")
+    del sbuf
 
 
 class Updater:
