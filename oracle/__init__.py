@@ -533,3 +533,129 @@ def sturm_count(chain, x) -> int:
     at_x = [sum(c * X ** t for t, c in enumerate(p)) for p in chain]
     at_minf = [c[-1] * (1 if (len(c) - 1) % 2 == 0 else -1) for c in chain]
     return sign_changes(at_minf) - sign_changes(at_x)
+
+
+# ---------------------------------------------------------------------------
+# The modified Sturm chain in secular form (Sec. 2.2, eqs. (4)-(9)), exact
+# ---------------------------------------------------------------------------
+def _frac_residues(lam, U, sigma):
+    """Exact alpha_j^{0} of eq. (4) from p_0 = pi_0 f_0 = det(xI - A'):
+    p_0(d_j) = -alpha_j prod_{k != j} (d_j - d_k)."""
+    from fractions import Fraction
+
+    lam = np.asarray(lam, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64).reshape(lam.shape[0], -1)
+    n, k = U.shape
+    S = _sig(sigma, k)
+    d = [Fraction(float(v)) for v in lam]
+    Uf = [[Fraction(float(U[i, c])) for c in range(k)] for i in range(n)]
+    A = [[(d[i] if i == j else Fraction(0)) + sum(Uf[i][c] * Uf[j][c] * int(S[c]) for c in range(k))
+          for j in range(n)] for i in range(n)]
+    alpha = []
+    for j in range(n):
+        pj = _frac_det([[(d[j] if r == c else 0) - A[r][c] for c in range(n)] for r in range(n)])
+        w = Fraction(1)
+        for t in range(n):
+            if t != j:
+                w *= d[j] - d[t]
+        alpha.append(-pj / w)
+    return d, alpha
+
+
+def _top3(c, alpha, poles):
+    """Coefficients of x^D, x^(D-1), x^(D-2) of (c - sum alpha_j/(x - d_j)) prod (x - d_k)."""
+    e1 = sum(poles)
+    e2 = (e1 * e1 - sum(p * p for p in poles)) / 2
+    return (c, -c * e1 - sum(alpha), c * e2 + sum(a * (e1 - p) for a, p in zip(alpha, poles)))
+
+
+def secular_sturm_chain(lam, U, sigma=None):
+    """The chain p_m = f_m pi_m, f_m = c_m - sum_{j <= N-m} alpha_j^{m}/(x - d_j),
+    pi_m = prod_{j <= N-m} (x - d_j), in exact rationals.
+
+    p_0 is eq. (5) with c_0 = 1; p_1 = p_0' in the form of eq. (6):
+    mu_j = 1 - sum_{i != j} (alpha_i + alpha_j)/(d_j - d_i), c_1 = sum mu_j,
+    alpha_j^{1} = (d_N - d_j) mu_j.  Then the secular long division:
+    p_m = A_m (x - B_m) p_{m-1} - p_{m-2} with A_m = c_{m-2}/c_{m-1} and B_m
+    chosen so that the x^(D-1) terms cancel (D = N-m+2 poles in p_{m-2}):
+    B_m = d_D + (1/c_{m-2}) sum alpha^{m-2} - (1/c_{m-1}) sum alpha^{m-1}.
+    The new residues follow from the values at the poles that remain:
+    alpha_j^{m} = A (d_j - B)(d_j - d_{D-1}) alpha_j^{m-1} - (d_j - d_{D-1})(d_j - d_D) alpha_j^{m-2},
+    and c_m is the x^(D-2) coefficient.  Returns (d, [(c_m, alpha^{m})]);
+    the chain stops early (returned shorter) if some c_m is 0."""
+    from fractions import Fraction
+
+    d, a0 = _frac_residues(lam, U, sigma)
+    N = len(d)
+    chain = [(Fraction(1), a0)]
+    if N == 0:
+        return d, chain
+    mu = [1 - sum((a0[i] + a0[j]) / (d[j] - d[i]) for i in range(N) if i != j) for j in range(N)]
+    chain.append((sum(mu), [(d[N - 1] - d[j]) * mu[j] for j in range(N - 1)]))
+    for m in range(2, N + 1):
+        c2, a2 = chain[m - 2]
+        c1, a1 = chain[m - 1]
+        if c1 == 0:
+            break
+        D = N - m + 2
+        A = c2 / c1
+        B = d[D - 1] + sum(a2) / c2 - sum(a1) / c1
+        t2 = _top3(c2, a2, d[:D])
+        t1 = _top3(c1, a1, d[:D - 1])
+        assert A * t1[0] - t2[0] == 0 and A * t1[1] - A * B * t1[0] - t2[1] == 0
+        cm = A * t1[2] - A * B * t1[1] - t2[2]
+        am = [A * (d[j] - B) * (d[j] - d[D - 2]) * a1[j] - (d[j] - d[D - 2]) * (d[j] - d[D - 1]) * a2[j]
+              for j in range(D - 2)]
+        chain.append((cm, am))
+    return d, chain
+
+
+def secular_sturm_values(d, chain, x):
+    """p_m(x) for every member of the secular chain (x exact; a pole uses the limit)."""
+    from fractions import Fraction
+
+    X = Fraction(float(x)) if not isinstance(x, Fraction) else x
+    out = []
+    for c, alpha in chain:
+        poles = d[:len(alpha)]
+        if any(X == p for p in poles):
+            j = poles.index(X)
+            w = Fraction(1)
+            for t, p in enumerate(poles):
+                if t != j:
+                    w *= X - p
+            out.append(-alpha[j] * w)
+            continue
+        f = c - sum(a / (X - p) for a, p in zip(alpha, poles))
+        pi = Fraction(1)
+        for p in poles:
+            pi *= X - p
+        out.append(f * pi)
+    return out
+
+
+def secular_sturm_count(d, chain, x) -> int:
+    """Distinct roots of p_0 below x: V(-inf) - V(x).  At -inf, p_m has the sign
+    of c_m (-1)^(number of its poles)."""
+    def changes(vals):
+        s = [v for v in vals if v != 0]
+        return sum(1 for a, b in zip(s, s[1:]) if (a > 0) != (b > 0))
+
+    at_minf = [c * (1 if len(a) % 2 == 0 else -1) for c, a in chain]
+    return changes(at_minf) - changes(secular_sturm_values(d, chain, x))
+
+
+def secular_deflate(lam, alpha, xi):
+    """Eq. (9): divide the roots xi_1..xi_s (found earlier) out of p_0, pairing
+    xi_p with the pole d_p: beta_j = alpha_j prod_p (d_j - d_p)/(d_j - xi_p) for
+    the poles j > s that remain, so that
+    p_0^1(x) = (1 - sum_{j>s} beta_j/(x - d_j)) prod_{j>s} (x - d_j) = p_0(x) / prod_p (x - xi_p)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    alpha = np.asarray(alpha, dtype=np.float64)
+    xi = np.asarray(xi, dtype=np.float64)
+    s = xi.shape[0]
+    rest = lam[s:]
+    beta = alpha[s:].copy()
+    for p in range(s):
+        beta *= (rest - lam[p]) / (rest - xi[p])
+    return rest, beta

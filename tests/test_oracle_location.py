@@ -143,3 +143,83 @@ def test_sturm_chain_of_a_known_polynomial():
     assert [float(c) for c in chain[0]] == [1.0, -2.0, 1.0]
     assert oracle.sturm_count(chain, 0.5) == 0
     assert oracle.sturm_count(chain, 1.5) == 1  # distinct roots only
+
+
+# --------------------------------------------------------------------------
+# The secular-form Sturm chain (eqs. (4)-(9))
+# --------------------------------------------------------------------------
+def _tiny(n, k, s, seed):
+    rng = np.random.default_rng(seed)
+    lam = np.sort(np.round(rng.standard_normal(n), 3))
+    U = np.round(rng.standard_normal((n, k)) * 0.5, 3)
+    return lam, U, np.array(s, dtype=np.int8)
+
+
+@pytest.mark.parametrize("n,k,s", [(4, 1, (1,)), (5, 2, (1, -1)), (6, 2, (-1, -1)), (6, 3, (1, 1, -1))])
+def test_secular_chain_equals_the_polynomial_remainder_chain(n, k, s):
+    """Secular long division yields -rem(p_{m-2}, p_{m-1}): every member equals
+    the polynomial Sturm chain's member exactly, at exact rational points."""
+    from fractions import Fraction
+
+    lam, U, sig = _tiny(n, k, s, 100 + n + k)
+    d, chain = oracle.secular_sturm_chain(lam, U, sig)
+    poly = oracle.sturm_chain(lam, U, sig)
+    assert len(chain) == n + 1 == len(poly)
+    for x in [Fraction(-7, 3), Fraction(1, 7), Fraction(22, 5), d[1] + Fraction(1, 1000)]:
+        vs = oracle.secular_sturm_values(d, chain, x)
+        vp = [sum(c * x ** t for t, c in enumerate(p)) for p in poly]
+        assert vs == vp
+
+
+@pytest.mark.parametrize("n,k,s", [(5, 1, (-1,)), (6, 2, (1, -1)), (7, 2, (1, 1)), (7, 4, (1, -1, 1, -1))])
+def test_secular_chain_counts_and_positive_leading_terms(n, k, s):
+    """A symmetric matrix has n real roots, so on a simple spectrum every c_m is
+    positive (the paper's test for a complete chain) and the chain's count
+    equals the dense and the inertia counts."""
+    lam, U, sig = _tiny(n, k, s, 300 + n * k)
+    d, chain = oracle.secular_sturm_chain(lam, U, sig)
+    w = np.linalg.eigvalsh(np.diag(lam) + (U * sig.astype(float)[None, :]) @ U.T)
+    assert np.min(np.diff(w)) > 1e-6  # simple spectrum
+    assert all(c > 0 for c, _ in chain)
+    rng = np.random.default_rng(n)
+    for x in np.concatenate([rng.uniform(w[0] - 1, w[-1] + 1, size=15), lam]):
+        if np.min(np.abs(w - x)) < 1e-9:
+            continue
+        ref = int(np.sum(w < x))
+        assert oracle.secular_sturm_count(d, chain, x) == ref
+        if not np.any(lam == x):
+            assert oracle.count(lam, U, sig, float(x)) == ref
+
+
+def test_exact_residues_agree_with_the_float_residues():
+    lam, U, sig = _tiny(7, 2, (1, -1), 9)
+    _, a_exact = oracle._frac_residues(lam, U, sig)
+    a = oracle.residues(lam, U, sig)
+    ref = np.array([float(v) for v in a_exact])
+    assert np.max(np.abs(a - ref) / np.abs(ref)) <= 1e-12
+
+
+def test_root_deflation_eq9():
+    """p_0^1(x) prod_p (x - xi_p) = p_0(x), and p_0^1 keeps the other roots."""
+    rng = np.random.default_rng(12)
+    n, k = 12, 2
+    lam = np.sort(rng.standard_normal(n))
+    U = rng.standard_normal((n, k)) * 0.5
+    sig = np.array([1, -1], dtype=np.int8)
+    A = np.diag(lam) + (U * sig.astype(float)[None, :]) @ U.T
+    w = np.linalg.eigvalsh(A)
+    alpha = oracle.residues(lam, U, sig)
+    for s in (1, 3, 5):
+        xi = w[:s]
+        rest, beta = oracle.secular_deflate(lam, alpha, xi)
+
+        def p01(x):
+            return (1.0 - np.sum(beta / (x - rest))) * np.prod(x - rest)
+
+        for x in rng.uniform(w[0] - 0.5, w[-1] + 0.5, size=10):
+            p0 = np.linalg.det(x * np.eye(n) - A)
+            scale = np.prod(np.abs(x - lam)) * (1 + np.sum(np.abs(alpha / (x - lam))))
+            assert abs(p01(x) * np.prod(x - xi) - p0) <= 1e-10 * scale
+        for r in w[s:]:
+            terms = np.abs(beta / (r - rest))
+            assert abs(1.0 - np.sum(beta / (r - rest))) <= 1e-9 * (1 + np.sum(terms))
