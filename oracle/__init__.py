@@ -659,3 +659,45 @@ def secular_deflate(lam, alpha, xi):
     for p in range(s):
         beta *= (rest - lam[p]) / (rest - xi[p])
     return rest, beta
+
+
+# ---------------------------------------------------------------------------
+# The first-order perturbation estimate (Sec. 3, eq. (11)): comparison method
+# ---------------------------------------------------------------------------
+def perturbation(Q, lam, K, sigma=None):
+    """mu_j = lam_j + u_j^T Sigma u_j and v_j = q_j + sum_{i != j}
+    (u_i^T Sigma u_j)/(lam_j - lam_i) q_i with u = rows of U = Q^T K (eq. (11)
+    read as standard first-order perturbation theory: the printed update names
+    v_j^0 and lam_i - lam_j where q_i and lam_j - lam_i belong).  Pairs with
+    lam_i == lam_j contribute nothing.  mu_j pairs with column j of X; nothing
+    is sorted."""
+    Q = np.asarray(Q, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    K = np.asarray(K, dtype=np.float64).reshape(lam.shape[0], -1)
+    s = _sig(sigma, K.shape[1]).astype(np.float64)
+    U = Q.T @ K
+    E = (U * s[None, :]) @ U.T  # E_ij = u_i^T Sigma u_j
+    n = lam.shape[0]
+    W = np.eye(n)
+    for j in range(n):
+        for i in range(n):
+            if i != j and lam[j] != lam[i]:
+                W[i, j] = E[i, j] / (lam[j] - lam[i])
+    mu = lam + np.diag(E)
+    return mu, Q @ W
+
+
+def fig67_metrics(Q, lam, K, sigma, mu, X):
+    """The accuracy panels of Figs. 6-7 for an estimate (mu, X) of the updated
+    pairs of A' = Q diag(lam) Q^T + K Sigma K^T: (A) 2-norm eigenvalue error
+    against the dense decomposition, relative to the 2-norm of the dense
+    eigenvalues; (B) 2-norm of A' - X diag(mu) X^T relative to ||A'||_2;
+    (C) 2-norm of X^T X - I."""
+    A = updated_matrix(Q, lam, K, sigma)
+    w = np.linalg.eigvalsh(A)
+    mu = np.asarray(mu, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    a = float(np.linalg.norm(np.sort(mu) - w) / np.linalg.norm(w))
+    b = float(np.linalg.norm(A - (X * mu[None, :]) @ X.T, 2) / np.linalg.norm(A, 2))
+    c = float(np.linalg.norm(X.T @ X - np.eye(X.shape[1]), 2))
+    return {"A": a, "B": b, "C": c}

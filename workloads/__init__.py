@@ -207,3 +207,16 @@ def poisson_arrivals(rate_per_s: float, count: int, seed: int) -> np.ndarray:
 def chained_K(n: int, k: int, seed: int) -> np.ndarray:
     rng = rng_for(seed)
     return rng.standard_normal((n, k)) / math.sqrt(n)
+
+
+def small_k(n: int = 100, k: int = 2, knorm: float = 0.01, seed: int = 5000, sigma="psd") -> dict:
+    """The Figs. 6-7 shape: N = 100 (by default), lam ~ U[-1,1] sorted, Q Haar,
+    K Gaussian rescaled to the 2-norm knorm (0.01 and 0.3 in the figures)."""
+    rng = rng_for(seed)
+    lam = _sorted_distinct_uniform(n, -1.0, 1.0, rng)
+    Q = haar(n, rng)
+    K = rng.standard_normal((n, k))
+    K *= knorm / np.linalg.norm(K, 2)
+    s = np.ones(k, dtype=np.int8) if sigma == "psd" else np.asarray(
+        random_sigma(k, rng, kminus=max(1, k // 2) if k > 1 else 0) if sigma == "mixed" else sigma, dtype=np.int8)
+    return dict(name="small_k_n%d_k%d" % (n, k), Q=Q, lam=lam, K=K, sigma=s)
