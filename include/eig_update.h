@@ -48,7 +48,9 @@ extern "C" {
 #define EIG_ENOTSUP (-6)  /* valid request this build does not implement */
 #define EIG_EBUSY (-7)    /* ticket not finished yet (eig_update_query) */
 #define EIG_ETOOBIG (-8)  /* problem larger than eig_secular_values_static's
-                             fixed scratch holds (n > EIG_STATIC_MAX_N) */
+                             fixed scratch holds (n > EIG_STATIC_MAX_N), or
+                             more selected pairs than eig_update_select's
+                             output holds (max_m) */
 
 #define EIG_MAX_K 16      /* largest rank this build accepts */
 
@@ -287,6 +289,44 @@ int eig_make_rank2(int64_t n, int64_t j, const double* a, double* K, int8_t* sig
    EIG_EINVAL for n < 2, NULL buffers or sigma entries other than +1/-1. */
 int eig_location_rank2(int64_t n, const double* lambda, const double* U, const int8_t* sigma,
                        double* alpha, int32_t* L, void* stream);
+
+/* Sec. 3, eq. (11): the first-order perturbation estimate the paper compares
+   against for a small K.  With U = Q^T K (u_j its rows):
+     mu_j = lambda_j + u_j^T Sigma u_j,
+     X    = Q W,  W_jj = 1,  W_ij = u_i^T Sigma u_j / (lambda_j - lambda_i)  (i != j),
+   with W_ij = 0 where lambda_i == lambda_j.  mu_j pairs with column j of X;
+   nothing is sorted or normalised.  Its error grows as |K|^4 (it is exact only to
+   first order): use it as the comparison the paper draws, not as an update.
+   Q (device n x n), lambda (device n), K (device n x k, k <= EIG_MAX_K), all
+   column-major; sigma host k entries of +1/-1 or NULL (all +1).  mu (device n)
+   may be lambda itself; X (device n x n) must not be Q.  X = Q W runs in the
+   handle's mode (FP64, or the split-BF16 tensor-core product in EIG_MIXED).
+   Uses the handle's workspace (n^2 doubles, plus slices in EIG_MIXED).
+   Synchronous on `stream`.  EIG_EINVAL for bad sizes, pointers or sigma,
+   EIG_ENOMEM when the workspace cannot grow, EIG_ETIMEOUT when a bounded
+   device wait gave up. */
+int eig_perturbation(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
+                     const double* K, const int8_t* sigma, double* mu, double* X, void* stream);
+
+/* Sec. 2.1 (only the eigenvalues of an interval) and Sec. 3 (a subset of the
+   eigenvectors): the eigenpairs of A' = Q diag(lambda) Q^T + K Sigma K^T whose
+   eigenvalues lie in [vl, vu), without the others.  Two counts give the
+   secular roots in the interval, the zero finder solves only those (pole
+   counts only at the poles around the interval), deflated pairs in the
+   interval are merged in, and X = Q W_sel (n x m) uses the FP64 GEMM in both
+   modes.  Q, lambda, K are read, not modified.
+   Q (device n x n), lambda (device n, ascending), K (device n x k), all
+   column-major; sigma host k entries or NULL.  mu (device max_m) receives the
+   m selected eigenvalues, ascending; X (device n x max_m, column-major, may
+   be NULL for values only) their unit eigenvectors (sign: largest entry of W's
+   column positive).  *m_out = m.  If m > max_m nothing is written and the
+   call returns EIG_ETOOBIG with *m_out = m (size the buffers and call again).
+   vl < vu required (use +-HUGE_VAL for half-open intervals).  Uses the
+   handle's workspace; synchronous on `stream`.  EIG_EINVAL / EIG_ENOMEM /
+   EIG_ENOTCONV / EIG_ETIMEOUT as eig_update_rank_k. */
+int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
+                      const double* K, const int8_t* sigma, double vl, double vu, int64_t max_m,
+                      double* mu, double* X, int64_t* m_out, void* stream);
 
 /* Library version string (static storage). */
 const char* eig_version(void);

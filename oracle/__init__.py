@@ -9,7 +9,8 @@ Plain and slow on purpose.  The C part (``orc.c``) holds the Jacobi
 eigensolver, the root count, the bisection root finder and the eq. (10)
 vectors.  This module composes them with numpy library primitives (matmul),
 and adds the rank-2 location vector (Algorithms 1a-1c, with the residues of
-eq. (3)) and the exact-rational Sturm chain of Sec. 2.2 for tiny problems.
+eq. (3)), the exact-rational Sturm chains of Sec. 2.2 for tiny problems, and
+the first-order perturbation estimate of eq. (11) with the Figs. 6-7 panels.
 Each function names the passage of the paper it follows.  The paper prints no
 worked example, so every pin is a closed form, an invariant, a special case or
 a library routine (``tests/test_oracle_pins.py``).
@@ -664,26 +665,29 @@ def secular_deflate(lam, alpha, xi):
 # ---------------------------------------------------------------------------
 # The first-order perturbation estimate (Sec. 3, eq. (11)): comparison method
 # ---------------------------------------------------------------------------
-def perturbation(Q, lam, K, sigma=None):
+def perturbation(Q, lam, K, sigma=None, cols=None):
     """mu_j = lam_j + u_j^T Sigma u_j and v_j = q_j + sum_{i != j}
     (u_i^T Sigma u_j)/(lam_j - lam_i) q_i with u = rows of U = Q^T K (eq. (11)
     read as standard first-order perturbation theory: the printed update names
     v_j^0 and lam_i - lam_j where q_i and lam_j - lam_i belong).  Pairs with
     lam_i == lam_j contribute nothing.  mu_j pairs with column j of X; nothing
-    is sorted."""
+    is sorted.  With cols, X holds only those columns (in that order)."""
     Q = np.asarray(Q, dtype=np.float64)
     lam = np.asarray(lam, dtype=np.float64)
     K = np.asarray(K, dtype=np.float64).reshape(lam.shape[0], -1)
     s = _sig(sigma, K.shape[1]).astype(np.float64)
     U = Q.T @ K
-    E = (U * s[None, :]) @ U.T  # E_ij = u_i^T Sigma u_j
     n = lam.shape[0]
-    W = np.eye(n)
-    for j in range(n):
+    cols = list(range(n)) if cols is None else [int(c) for c in cols]
+    W = np.zeros((n, len(cols)))
+    for t, j in enumerate(cols):
+        e_j = U @ (s * U[j])  # E_ij = u_i^T Sigma u_j for every i
         for i in range(n):
-            if i != j and lam[j] != lam[i]:
-                W[i, j] = E[i, j] / (lam[j] - lam[i])
-    mu = lam + np.diag(E)
+            if i == j:
+                W[i, t] = 1.0
+            elif lam[j] != lam[i]:
+                W[i, t] = e_j[i] / (lam[j] - lam[i])
+    mu = lam + np.einsum("ic,c,ic->i", U, s, U)
     return mu, Q @ W
 
 

@@ -25,6 +25,7 @@ __all__ = [
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
     "eig_server_poll", "eig_server_query", "eig_server_pending", "Server", "eig_location_rank2",
+    "eig_perturbation", "eig_update_select",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
@@ -117,6 +118,9 @@ def lib() -> ctypes.CDLL:
         L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
         L.eig_make_rank2.argtypes = [i64, i64, vp, vp, vp, vp]
         L.eig_location_rank2.argtypes = [i64, vp, vp, vp, vp, vp, vp]
+        L.eig_perturbation.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.eig_update_select.argtypes = [vp, i64, i32, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i64,
+                                        vp, vp, ctypes.POINTER(i64), vp]
         L.eig_secular_values_static.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp]
         L.eig_server_create.argtypes = [ctypes.POINTER(eig_server_params), ctypes.POINTER(vp)]
         L.eig_server_destroy.argtypes = [vp]
@@ -131,7 +135,8 @@ def lib() -> ctypes.CDLL:
         L.eig_version.restype = ctypes.c_char_p
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
                   "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
-                  "eig_secular_values_static", "eig_location_rank2"):
+                  "eig_secular_values_static", "eig_location_rank2", "eig_perturbation",
+                  "eig_update_select"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -340,6 +345,36 @@ def eig_location_rank2(lam, U, sigma, alpha, L, stream=None) -> None:
     _check(lib().eig_location_rank2(n, _ptr(lam, "lambda"), _ptr(U, "U", True), sp, _ptr(alpha, "alpha"),
                                     ctypes.c_void_p(L.data_ptr()), _stream(stream)), "eig_location_rank2")
     del sbuf
+
+
+def eig_perturbation(h, Q, lam, K, sigma, mu, X, stream=None) -> None:
+    """First-order estimate of eq. (11): mu (device n) and X = Q W (device n x n,
+    column-major); mu_j pairs with column j of X."""
+    n = int(Q.shape[0])
+    k = int(K.shape[1])
+    sbuf, sp = _sigma_buf(sigma, k)
+    _check(lib().eig_perturbation(h, n, k, _ptr(Q, "Q", True), _ptr(lam, "lambda"), _ptr(K, "K", True), sp,
+                                  _ptr(mu, "mu"), _ptr(X, "X", True), _stream(stream)), "eig_perturbation")
+    del sbuf
+
+
+def eig_update_select(h, Q, lam, K, sigma, vl, vu, mu, X=None, stream=None):
+    """Eigenpairs of A' with eigenvalues in [vl, vu): mu (device, capacity
+    max_m = len(mu)) and X (device n x max_m column-major, or None).  Returns
+    (status, m); EIG_ETOOBIG (nothing written) when m > max_m."""
+    n = int(Q.shape[0])
+    k = int(K.shape[1])
+    max_m = int(mu.shape[0])
+    if X is not None and (int(X.shape[0]) != n or int(X.shape[1]) < max_m):
+        raise ValueError("X must be n x max_m")
+    sbuf, sp = _sigma_buf(sigma, k)
+    m = ctypes.c_int64()
+    rc = lib().eig_update_select(h, n, k, _ptr(Q, "Q", True), _ptr(lam, "lambda"), _ptr(K, "K", True), sp,
+                                 float(vl), float(vu), max_m, _ptr(mu, "mu"),
+                                 _ptr(X, "X", True) if X is not None else None, ctypes.byref(m), _stream(stream))
+    del sbuf
+    _check(rc, "eig_update_select", ok=(EIG_OK, EIG_ENOTCONV, EIG_ETOOBIG))
+    return rc, int(m.value)
 
 
 class Updater:

@@ -869,6 +869,135 @@ int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda,
   return status_of(*h->st_host);
 }
 
+int eig_perturbation(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
+                     const double* K, const int8_t* sigma, double* mu, double* X, void* stream) {
+  if (!h || n < 1 || k < 1 || k > EIG_MAX_K || !Q || !lambda || !K || !mu || !X ||
+      n > (int64_t)0x3fffffff || X == Q)
+    return EIG_EINVAL;
+  unsigned long long negmask = 0;
+  int kplus = 0;
+  if (!sigma_info(sigma, k, &negmask, &kplus)) return EIG_EINVAL;
+  DeviceGuard g(h->device);
+  if (!g.ok) return EIG_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool mixed = (h->mode == EIG_MIXED);
+  // workspace: status, U, W (or W^T), and in mixed mode the slices of Q and W^T
+  auto layout = [&](char* base, DevStatus** st, double** U, double** W, __nv_bfloat16** Qs,
+                    __nv_bfloat16** Ws, unsigned long long** rmax, int** erow, int** fcol) {
+    Bump b(base);
+    *st = reinterpret_cast<DevStatus*>(b.take(sizeof(DevStatus)));
+    *U = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * k));
+    *W = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * n));
+    if (mixed) {
+      const size_t planes = 2 * (size_t)tc_num_slices() * tc_slice_plane((int)n);
+      *Qs = reinterpret_cast<__nv_bfloat16*>(b.take(planes));
+      *Ws = reinterpret_cast<__nv_bfloat16*>(b.take(planes));
+      *rmax = reinterpret_cast<unsigned long long*>(b.take(sizeof(unsigned long long) * (size_t)n));
+      *erow = reinterpret_cast<int*>(b.take(sizeof(int) * (size_t)n));
+      *fcol = reinterpret_cast<int*>(b.take(sizeof(int) * (size_t)n));
+    }
+    return b.off;
+  };
+  DevStatus* st = nullptr;
+  double *U = nullptr, *W = nullptr;
+  __nv_bfloat16 *Qs = nullptr, *Ws = nullptr;
+  unsigned long long* rmax = nullptr;
+  int *erow = nullptr, *fcol = nullptr;
+  const size_t need = layout(nullptr, &st, &U, &W, &Qs, &Ws, &rmax, &erow, &fcol);
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  layout(h->ws, &st, &U, &W, &Qs, &Ws, &rmax, &erow, &fcol);
+  CK(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+  CK(launch_project_f64(n, k, Q, K, U, s));
+  CK(launch_perturb_w(n, k, lambda, U, negmask, mixed, W, s));
+  CK(launch_perturb_mu(n, k, lambda, U, negmask, mu, s));  // after W: mu may alias lambda
+  if (mixed) {
+    CK(launch_slice_q((int)n, W, rmax, fcol, Ws, nullptr, s));  // rows of W^T = columns of W
+    CK(launch_slice_q((int)n, Q, rmax, erow, Qs, nullptr, s));
+    CK(launch_gemm_tc((int)n, Qs, Ws, erow, fcol, X, (int)n, nullptr, &st->flags, s));
+  } else {
+    CK(launch_gemm_f64(n, n, n, Q, n, W, n, X, n, s));
+  }
+  CK(cudaMemcpyAsync(h->st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return status_of(*h->st_host);
+}
+
+int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
+                      const double* K, const int8_t* sigma, double vl, double vu, int64_t max_m,
+                      double* mu, double* X, int64_t* m_out, void* stream) {
+  if (!h || n < 1 || k < 1 || k > EIG_MAX_K || !Q || !lambda || !K || !mu || !m_out || max_m < 0 ||
+      n > (int64_t)0x3fffffff || !(vl < vu))
+    return EIG_EINVAL;
+  unsigned long long negmask = 0;
+  int kplus = 0;
+  if (!sigma_info(sigma, k, &negmask, &kplus)) return EIG_EINVAL;
+  DeviceGuard g(h->device);
+  if (!g.ok) return EIG_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int Kp = padded_rank(k);
+  const int ld = (int)align_up((size_t)n, 32);
+  const size_t cap = (size_t)(max_m < n ? max_m : n);
+  // workspace: the secular carve (values only) + window ints + W_sel
+  const size_t base = align_up(plan(nullptr, n, k, false, false, false).bytes, 256);
+  const size_t need = base + 256 + (X ? sizeof(double) * (size_t)n * (cap > 0 ? cap : 1) : 0);
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  Carve c = plan(h->ws, n, k, false, false, false);
+  int* win = reinterpret_cast<int*>(h->ws + base);               // 8 ints + 2 count slots
+  double* pts = reinterpret_cast<double*>(h->ws + base + 128);    // vl, vu
+  double* Wsel = X ? reinterpret_cast<double*>(h->ws + base + 256) : nullptr;
+  const double xv[2] = {vl, vu};
+  CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
+  CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
+  CK(launch_project_f64(n, k, Q, K, c.U, s));
+  CK(launch_deflate(n, k, Kp, lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
+                    c.lam_defl, c.st, s));
+  Sub sub;
+  sub.n_dev = &c.st->n_keep;
+  sub.ld = ld;
+  sub.K = Kp;
+  sub.kplus = kplus + (Kp - k);
+  sub.lam = c.lam_keep;
+  sub.Us = c.Us;
+  sub.idx = c.idx_keep;
+  sub.st = c.st;
+  sub.negmask = negmask;
+  CK(launch_counts(sub, pts, 2, win + 8, s));
+  CK(launch_select_window(sub, c.st, c.lam_defl, vl, vu, win + 8, win, s));
+  int hw[8];
+  CK(cudaMemcpyAsync(hw, win, sizeof(hw), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h->st_host->flags & (ST_UNSORTED | ST_NONFINITE)) return EIG_EINVAL;
+  const int nk = hw[6];
+  int r0 = hw[0], r1 = hw[1];
+  r0 = r0 < 0 ? 0 : (r0 > nk ? nk : r0);
+  r1 = r1 < r0 ? r0 : (r1 > nk ? nk : r1);
+  const int qa = hw[2], qb = hw[3], dlo = hw[4], dsel = hw[5];
+  const int64_t m = (int64_t)(r1 - r0) + dsel;
+  *m_out = m;
+  if (m > max_m) return EIG_ETOOBIG;
+  if (m == 0) return EIG_OK;
+  if (r1 > r0) {
+    // true pole counts around the interval, placeholders elsewhere
+    const int p0 = qa > 0 ? qa - 1 : 0;
+    const int p1 = qb < nk ? qb + 1 : nk;
+    CK(launch_select_fill(nk, p0, p1, c.pole_cnt, s));
+    CK(launch_counts(sub, nullptr, ld, c.pole_cnt, s, p0, p1));
+    CK(cudaMemcpyAsync(c.counter, &r0, sizeof(int), cudaMemcpyHostToDevice, s));
+    RootOut ro{c.origin, c.tau, c.iters, c.rflags, c.alpha, c.beta, c.sidx};
+    CK(launch_roots(sub, c.pole_cnt, h->max_iter, c.counter, ro, c.st, h->num_sms, s, r1 - r0, r1));
+  }
+  if (Wsel) CK(cudaMemsetAsync(Wsel, 0, sizeof(double) * (size_t)n * (size_t)m, s));
+  RootOut ro{c.origin, c.tau, c.iters, c.rflags, c.alpha, c.beta, c.sidx};
+  CK(launch_assemble_select(sub, ro, n, c.idx_defl, c.lam_defl, dlo, dsel, r0, r1, c.mu_sec, mu, Wsel, s));
+  if (X) CK(launch_gemm_f64(n, m, n, Q, n, Wsel, n, X, n, s));
+  CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return status_of(*h->st_host);
+}
+
 int eig_make_rank2(int64_t n, int64_t j, const double* a, double* K, int8_t* sigma, void* stream) {
   if (n < 1 || j < 0 || j >= n || !a || !K || !sigma) return EIG_EINVAL;
   sigma[0] = 1;

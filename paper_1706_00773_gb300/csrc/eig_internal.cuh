@@ -229,11 +229,15 @@ cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const dou
                            unsigned long long negmask, double* lam_keep, double* Us, int ld,
                            int* idx_keep, int* idx_defl, double* lam_defl, DevStatus* st,
                            cudaStream_t s);
-// Root counts #{mu < x}: at every pole of the sub-problem (x == nullptr,
-// npts = ld, points past n' skipped) or at npts absolute points x.
-cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s);
+// Root counts #{mu < x}: at the poles [pt0, min(n', pt_end)) of the sub-problem
+// (x == nullptr; counts[q] for pole q) or at npts absolute points x.
+cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s,
+                          int pt0 = 0, int pt_end = 0x7fffffff);
+// Zero finder over the roots [*work_counter, min(n', m_end)); m_count (an upper
+// bound on how many, -1 = ld) sizes the grid.
 cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int* work_counter,
-                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s);
+                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s,
+                         int m_count = -1, int m_end = 0x7fffffff);
 // mu of every secular root, output positions, new eigenvalues (ascending,
 // merged with the deflated ones) and, when W != nullptr, the eq. (10) columns
 // of W (n x n, column-major, zero-filled beforehand by the caller).
@@ -241,12 +245,29 @@ cudaError_t launch_assemble(const Sub& sub, const RootOut& roots, int64_t n, con
                             const double* lam_defl, const DevStatus* st, double* mu_sec,
                             double* lam_out, double* W, cudaStream_t s,
                             const WSlices& ws = WSlices());
+// Eigenpairs in [vl, vu) (secular.cu): the window of counts and indices (8 ints,
+// see select_window_kernel), placeholder pole counts outside the pole window
+// [p0, p1), and the assembly of the selected pairs into mu_out (ascending) and
+// W (n x m, zero-filled beforehand; may be null).
+cudaError_t launch_select_window(const Sub& sub, const DevStatus* st, const double* lam_defl, double vl,
+                                 double vu, const int* c2, int* out, cudaStream_t s);
+cudaError_t launch_select_fill(int nk, int p0, int p1, int* pole_cnt, cudaStream_t s);
+cudaError_t launch_assemble_select(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
+                                   const double* lam_defl, int dlo, int dsel, int r0, int r1, double* mu_sec,
+                                   double* mu_out, double* W, cudaStream_t s);
 cudaError_t launch_gemm_f64(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                             const double* B, int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
 // Same, but skipped on the device when st reports invalid input.
 cudaError_t launch_gemm_f64_guarded(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                                     const double* B, int64_t ldb, double* C, int64_t ldc,
                                     const DevStatus* st, cudaStream_t s);
+// First-order perturbation estimate of eq. (11) (perturb.cu).  W = I + E with
+// E_ij = u_i^T Sigma u_j / (lam_j - lam_i) (0 where lam_i == lam_j), written
+// column-major, or as W^T column-major when transposed.  mu_j = lam_j + u_j^T Sigma u_j.
+cudaError_t launch_perturb_w(int64_t n, int k, const double* lam, const double* U, unsigned long long negmask,
+                             bool transposed, double* W, cudaStream_t s);
+cudaError_t launch_perturb_mu(int64_t n, int k, const double* lam, const double* U, unsigned long long negmask,
+                              double* mu, cudaStream_t s);
 // Small helpers (util.cu).
 cudaError_t launch_copy_guarded(double* dst, const double* src, int64_t count, const DevStatus* st,
                                 cudaStream_t s);

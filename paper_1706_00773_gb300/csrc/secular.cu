@@ -358,7 +358,8 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
 
 template <int K>
 __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __restrict__ xs,
-                                                     int npts, int* __restrict__ counts) {
+                                                     int npts, int* __restrict__ counts, int pt0,
+                                                     int pt_end) {
   constexpr int E = warps_per_root(K);
   constexpr int G = 4 / E;
   constexpr int KP = K + 1;
@@ -369,9 +370,11 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
   if (input_invalid(sub.st)) return;
   const int n = *sub.n_dev;
   const bool absolute = (xs != nullptr);
-  const int limit = absolute ? npts : n;
+  // Pole mode covers the poles [pt0, min(n, pt_end)).
+  const int first = absolute ? 0 : pt0;
+  const int limit = absolute ? npts : min(n, pt_end);
   // Every group runs the same number of trips so that the named barriers match.
-  for (int base = blockIdx.x * G; base < limit; base += gridDim.x * G) {
+  for (int base = first + blockIdx.x * G; base < limit; base += gridDim.x * G) {
     const int pt = base + g;
     const bool active = pt < limit;
     const double tau = (active && absolute) ? xs[pt] : 0.0;
@@ -694,6 +697,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
         conv = true;
         notconv = true;
       }
+      const double delta = tn - tau;  // the accepted point minus the evaluated one
       tau = tn;
       if (conv) {
         // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
@@ -706,10 +710,39 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
             jmin = j;
           }
         }
-        if (lane < K) out.alpha[(size_t)m * K + lane] = V[lane * ZP + jmin];
+        // Z was diagonalised at the evaluated point; the root is delta away
+        // (an accepted Newton step or a bisection midpoint).  Move the null
+        // vector there to first order: v += delta sum_j (v_j^T Z' v)/(z_min - z_j) v_j
+        // with Z' = diag(N^, 1, 1).  A term that is not small (a nearly
+        // repeated zero eigenvalue) is left out.
+        double comp = (lane < Z2) ? V[lane * ZP + jmin] : 0.0;
+        if (delta != 0.0) {
+          double gam = 0.0;
+          if (lane < Z2 && lane != jmin) {
+            double q = 0.0;
+            for (int a = 0; a < K; ++a) {
+              double na = 0.0;
+              for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + jmin], na);
+              q = fma(V[a * ZP + lane], na, q);
+            }
+            if (has_a) q = fma(V[K * ZP + lane], V[K * ZP + jmin], q);
+            if (has_b) q = fma(V[(K + 1) * ZP + lane], V[(K + 1) * ZP + jmin], q);
+            gam = delta * q / (Z[jmin * ZP + jmin] - Z[lane * ZP + lane]);
+            if (!(fabs(gam) <= 1e-3)) gam = 0.0;
+          }
+          double acc = comp;
+          for (int j = 0; j < Z2; ++j) {
+            const double gj = __shfl_sync(0xffffffffu, gam, j);
+            if (lane < Z2) acc = fma(gj, V[lane * ZP + j], acc);
+          }
+          comp = acc;
+        }
+        const double beta_a = __shfl_sync(0xffffffffu, comp, K);
+        const double beta_b = __shfl_sync(0xffffffffu, comp, K + 1);
+        if (lane < K) out.alpha[(size_t)m * K + lane] = comp;
         if (lane == 0) {
-          out.beta[2 * (size_t)m] = V[K * ZP + jmin];
-          out.beta[2 * (size_t)m + 1] = V[(K + 1) * ZP + jmin];
+          out.beta[2 * (size_t)m] = beta_a;
+          out.beta[2 * (size_t)m + 1] = beta_b;
           out.sidx[2 * (size_t)m] = ia;
           out.sidx[2 * (size_t)m + 1] = ib;
           out.origin[m] = o;
@@ -738,7 +771,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
 template <int K>
 __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restrict__ pole_cnt,
                                                     int max_iter, int* counter, RootOut out,
-                                                    DevStatus* st) {
+                                                    DevStatus* st, int m_end) {
   constexpr int E = warps_per_root(K);
   constexpr int G = 4 / E;
   constexpr int KP = K + 1;
@@ -751,11 +784,12 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
   const int n = *sub.n_dev;
+  const int stop = min(n, m_end);  // roots [*counter at launch, stop)
   for (;;) {
     if (e == 0 && lane == 0) s_m[g] = atomicAdd(counter, 1);
     group_sync<E>(g);
     const int m = s_m[g];
-    if (m >= n) break;
+    if (m >= stop) break;
     root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
                   &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], g, e, lane);
   }
@@ -849,10 +883,10 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
                                               const double* __restrict__ mu_sec,
                                               double* __restrict__ lam_out, double* __restrict__ W,
                                               const WSlices& ws, int m, double* s_n2, double* s_mx,
-                                              int* s_ix) {
+                                              int* s_ix, int64_t pos_shift = 0) {
   const int t = threadIdx.x;
   const double mu = mu_sec[m];
-  const int64_t pos = m + lower_bound_d(lam_defl, nd, mu);
+  const int64_t pos = m + lower_bound_d(lam_defl, nd, mu) - pos_shift;
   if (t == 0) lam_out[pos] = mu;
   if (!W && !ws.Ws) return;
   const int o = roots.origin[m];
@@ -1021,23 +1055,106 @@ __global__ void class_prefix_kernel(const ProbDesc* __restrict__ P, ClassDesc c)
   *c.counter = 0;
 }
 
+// ---- eigenpairs in a value interval [vl, vu) ------------------------------------
+// out: r0 = #{mu' < vl}, r1 = #{mu' < vu} (secular roots, from the two counts),
+// qa / qb = first pole >= vl / >= vu, dlo / dsel = first deflated value >= vl
+// and how many lie in [vl, vu), n', n_defl.
+__global__ void select_window_kernel(Sub sub, const DevStatus* st, const double* __restrict__ lam_defl,
+                                     double vl, double vu, const int* __restrict__ c2, int* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (input_invalid(st)) {
+    for (int i = 0; i < 8; ++i) out[i] = 0;
+    return;
+  }
+  const int nk = *sub.n_dev, nd = st->n_defl;
+  const int dlo = lower_bound_d(lam_defl, nd, vl), dhi = lower_bound_d(lam_defl, nd, vu);
+  out[0] = c2[0];
+  out[1] = c2[1];
+  out[2] = lower_bound_d(sub.lam, nk, vl);
+  out[3] = lower_bound_d(sub.lam, nk, vu);
+  out[4] = dlo;
+  out[5] = dhi > dlo ? dhi - dlo : 0;
+  out[6] = nk;
+  out[7] = nd;
+}
+
+// Poles outside [p0, p1) get counts that keep the placement of every root in
+// [r0, r1) unchanged: 0 below (their true count is <= r0) and n' above (>= r1).
+__global__ void select_fill_kernel(int nk, int p0, int p1, int* __restrict__ pole_cnt) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nk; q += gridDim.x * blockDim.x) {
+    if (q < p0) pole_cnt[q] = 0;
+    else if (q >= p1) pole_cnt[q] = nk;
+  }
+}
+
+__global__ void mu_select_kernel(Sub sub, RootOut roots, int r0, int r1, double* __restrict__ mu_sec) {
+  for (int m = r0 + blockIdx.x * blockDim.x + threadIdx.x; m < r1; m += gridDim.x * blockDim.x)
+    mu_sec[m] = sub.lam[roots.origin[m]] + roots.tau[m];
+}
+
+// Selected secular roots: position (m - r0) + #{selected deflated values < mu}.
+template <int K>
+__global__ void __launch_bounds__(kAsmThreads) assemble_select_kernel(
+    Sub sub, RootOut roots, int64_t n, const double* __restrict__ lam_dsel, int dsel, int r0, int r1,
+    const double* __restrict__ mu_sec, double* __restrict__ mu_out, double* __restrict__ W) {
+  __shared__ double s_n2[kAsmThreads];
+  __shared__ double s_mx[kAsmThreads];
+  __shared__ int s_ix[kAsmThreads];
+  const int nk = *sub.n_dev;
+  for (int m = r0 + blockIdx.x; m < r1; m += gridDim.x) {
+    assemble_root<K>(sub, roots, n, lam_dsel, dsel, nk, mu_sec, mu_out, W, WSlices(), m, s_n2, s_mx, s_ix,
+                     r0);
+    __syncthreads();
+  }
+}
+
+// Selected deflated pairs: position j + #{selected secular roots <= lam}, W column e_i.
+__global__ void deflated_select_kernel(int64_t n, const int* __restrict__ idx_dsel,
+                                       const double* __restrict__ lam_dsel, int dsel,
+                                       const double* __restrict__ mu_sel, int nsel,
+                                       double* __restrict__ mu_out, double* __restrict__ W) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < dsel; j += gridDim.x * blockDim.x) {
+    const double v = lam_dsel[j];
+    const int64_t pos = j + upper_bound_d(mu_sel, nsel, v);
+    mu_out[pos] = v;
+    if (W) W[(int64_t)idx_dsel[j] + pos * n] = 1.0;
+  }
+}
+
+template <int K>
+cudaError_t launch_assemble_select_k(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
+                                     const double* lam_defl, int dlo, int dsel, int r0, int r1,
+                                     double* mu_sec, double* mu_out, double* W, cudaStream_t s) {
+  const int cnt = r1 - r0;
+  if (cnt > 0) {
+    mu_select_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(sub, roots, r0, r1, mu_sec);
+    assemble_select_kernel<K><<<cnt < 65535 ? cnt : 65535, kAsmThreads, 0, s>>>(
+        sub, roots, n, lam_defl + dlo, dsel, r0, r1, mu_sec, mu_out, W);
+  }
+  if (dsel > 0)
+    deflated_select_kernel<<<(dsel + 255) / 256, 256, 0, s>>>(n, idx_defl + dlo, lam_defl + dlo, dsel,
+                                                              mu_sec + r0, cnt, mu_out, W);
+  return cudaGetLastError();
+}
+
 int g_occ_roots[17];
 
 template <int K>
 cudaError_t launch_counts_k(const Sub& sub, const double* x, int npts, int* counts,
-                            cudaStream_t s) {
+                            cudaStream_t s, int pt0, int pt_end) {
   constexpr int G = 4 / warps_per_root(K);
-  const int pts = x ? npts : sub.ld;
+  const int pts = x ? npts : min(sub.ld, pt_end) - pt0;
   int blocks = (pts + G - 1) / G;
   if (blocks < 1) blocks = 1;
   if (blocks > 65535) blocks = 65535;
-  counts_kernel<K><<<blocks, 128, 0, s>>>(sub, x, npts, counts);
+  counts_kernel<K><<<blocks, 128, 0, s>>>(sub, x, npts, counts, pt0, pt_end);
   return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t launch_roots_k(const Sub& sub, const int* pole_cnt, int max_iter, int* counter,
-                           const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s) {
+                           const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s,
+                           int m_count, int m_end) {
   constexpr int G = 4 / warps_per_root(K);
   if (g_occ_roots[K] == 0) {
     int occ = 0;
@@ -1045,11 +1162,11 @@ cudaError_t launch_roots_k(const Sub& sub, const int* pole_cnt, int max_iter, in
     if (e != cudaSuccess) return e;
     g_occ_roots[K] = occ > 0 ? occ : 1;
   }
-  long long want = ((long long)sub.ld + G - 1) / G;
+  long long want = ((long long)m_count + G - 1) / G;
   long long cap = (long long)num_sms * g_occ_roots[K];
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
-  roots_kernel<K><<<blocks, 128, 0, s>>>(sub, pole_cnt, max_iter, counter, out, st);
+  roots_kernel<K><<<blocks, 128, 0, s>>>(sub, pole_cnt, max_iter, counter, out, st, m_end);
   return cudaGetLastError();
 }
 
@@ -1071,30 +1188,50 @@ cudaError_t launch_assemble_k(const Sub& sub, const RootOut& roots, int64_t n,
 
 }  // namespace
 
-cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s) {
+cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s,
+                          int pt0, int pt_end) {
+  if (!x && pt0 < 0) return cudaErrorInvalidValue;
+  if (!x && pt_end <= pt0) return cudaSuccess;  // empty window
   switch (sub.K) {
-    case 1: return launch_counts_k<1>(sub, x, npts, counts, s);
-    case 2: return launch_counts_k<2>(sub, x, npts, counts, s);
-    case 3: return launch_counts_k<3>(sub, x, npts, counts, s);
-    case 4: return launch_counts_k<4>(sub, x, npts, counts, s);
-    case 5: return launch_counts_k<5>(sub, x, npts, counts, s);
-    case 6: return launch_counts_k<6>(sub, x, npts, counts, s);
-    case 7: return launch_counts_k<7>(sub, x, npts, counts, s);
-    case 8: return launch_counts_k<8>(sub, x, npts, counts, s);
-    case 10: return launch_counts_k<10>(sub, x, npts, counts, s);
-    case 12: return launch_counts_k<12>(sub, x, npts, counts, s);
-    case 14: return launch_counts_k<14>(sub, x, npts, counts, s);
-    case 16: return launch_counts_k<16>(sub, x, npts, counts, s);
+#define C_(K_) case K_: return launch_counts_k<K_>(sub, x, npts, counts, s, pt0, pt_end);
+    C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(10) C_(12) C_(14) C_(16)
+#undef C_
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_roots(const Sub& sub, const int* pole_cnt, int max_iter, int* counter,
-                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s) {
+                         const RootOut& out, DevStatus* st, int num_sms, cudaStream_t s,
+                         int m_count, int m_end) {
+  if (m_count < 0) m_count = sub.ld;
   switch (sub.K) {
-#define R_(K_) case K_: return launch_roots_k<K_>(sub, pole_cnt, max_iter, counter, out, st, num_sms, s);
+#define R_(K_) case K_: return launch_roots_k<K_>(sub, pole_cnt, max_iter, counter, out, st, num_sms, s, m_count, m_end);
     R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8) R_(10) R_(12) R_(14) R_(16)
 #undef R_
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_select_window(const Sub& sub, const DevStatus* st, const double* lam_defl, double vl,
+                                 double vu, const int* c2, int* out, cudaStream_t s) {
+  select_window_kernel<<<1, 32, 0, s>>>(sub, st, lam_defl, vl, vu, c2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select_fill(int nk, int p0, int p1, int* pole_cnt, cudaStream_t s) {
+  if (nk <= 0) return cudaSuccess;
+  const int blocks = (nk + 255) / 256 < 4096 ? (nk + 255) / 256 : 4096;
+  select_fill_kernel<<<blocks, 256, 0, s>>>(nk, p0, p1, pole_cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_select(const Sub& sub, const RootOut& roots, int64_t n, const int* idx_defl,
+                                   const double* lam_defl, int dlo, int dsel, int r0, int r1, double* mu_sec,
+                                   double* mu_out, double* W, cudaStream_t s) {
+  switch (sub.K) {
+#define S_(K_) case K_: return launch_assemble_select_k<K_>(sub, roots, n, idx_defl, lam_defl, dlo, dsel, r0, r1, mu_sec, mu_out, W, s);
+    S_(1) S_(2) S_(3) S_(4) S_(5) S_(6) S_(7) S_(8) S_(10) S_(12) S_(14) S_(16)
+#undef S_
     default: return cudaErrorInvalidValue;
   }
 }

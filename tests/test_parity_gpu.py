@@ -362,3 +362,19 @@ def test_batch_mixes_values_only_and_invalid(eu, handle):
         assert np.max(np.abs(host(d["lam"]) - ref["mu"])) <= MU_TOL * norm2_A(P["lam"], P["K"])
         if i % 2:
             assert np.array_equal(host(d["Q"]), P["Q"])  # values only: Q untouched
+
+
+def test_residuals_at_rounding_level(eu, handle):
+    """The null vector is taken at the accepted root, not at the last evaluated
+    point (a Newton step away), so eq. (10) vectors reach rounding-level
+    residuals like the oracle's; includes a problem with planted deflation."""
+    import torch
+
+    P = workloads.general(400, 3, seed=71, sigma="mixed", lam_kind="uniform")
+    Q = P["Q"]
+    P["K"] = P["K"] - Q[:, 50:60] @ (Q[:, 50:60].T @ P["K"])
+    for prob in (P, workloads.general(700, 8, seed=72, sigma="psd", lam_kind="logspec")):
+        rc, rep, mu, X = _run_update(eu, handle, prob, want=eu.EIG_VALUES | eu.EIG_VECTORS)
+        assert rc == 0
+        res = oracle.residuals(prob["Q"], prob["lam"], prob["K"], prob["sigma"], mu, X)
+        assert np.max(res) <= 1e-13 * norm2_A(prob["lam"], prob["K"])
