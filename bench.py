@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-update batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving measurement")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the interval query, eq. (11) and rank-1 chain comparisons")
     return ap.parse_args()
 
 
@@ -383,6 +385,110 @@ def run_serving(eu, dev, mode, residents=12, nmin=1024, nmax=4096, chain=6, load
                             residents, nmin, nmax, chain, load)}
 
 
+def _time_ms(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    out = []
+    for _ in range(reps):
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def run_comparisons(eu, dev, mode, P, full_ms):
+    """What the paper sets beside the update: an interval of the spectrum only
+    (Sec. 2.1 / Sec. 3 subsets), the first-order estimate of eq. (11) with the
+    accuracy panels of Figs. 6-7 (direct decomposition = LAPACK on the dense
+    matrix), and two successive rank-1 updates against one rank-2 update
+    (Fig. 4)."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    out = {}
+    n, k = P["Q"].shape[0], P["K"].shape[1]
+    h = eu.eig_update_init(dev.index or 0, mode)
+    Q = torch.from_numpy(np.asfortranarray(P["Q"])).to(dev)
+    lam = torch.from_numpy(P["lam"].copy()).to(dev)
+    K = torch.from_numpy(np.asfortranarray(P["K"])).to(dev)
+    # interval query: about 1% of the spectrum from its middle, with vectors
+    lo, hi = n // 2 - n // 200, n // 2 + n // 200
+    vl, vu = float(P["lam"][lo]), float(P["lam"][hi])
+    mu = torch.empty(n, dtype=torch.float64, device=dev)
+    X = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    res = {}
+
+    def sel():
+        res["rc"], res["m"] = eu.eig_update_select(h, Q, lam, K, P["sigma"], vl, vu, mu, X)
+
+    ms = _time_ms(sel, 3)
+    out["interval_query"] = {"pairs": res["m"], "ms": ms, "full_update_ms": full_ms,
+                             "speedup_vs_full": full_ms / ms, "interval": "eigenvalues in [lam[%d], lam[%d])" % (lo, hi)}
+    # eq. (11) at the same size, in the same arithmetic mode
+    Xp = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    mup = torch.empty(n, dtype=torch.float64, device=dev)
+    out["perturbation"] = {"ms": _time_ms(lambda: eu.eig_perturbation(h, Q, lam, K, P["sigma"], mup, Xp), 3),
+                           "full_update_ms": full_ms}
+    del Q, K, X, Xp
+    panels = []
+    for knorm in (0.01, 0.3):
+        for kk in (1, 2, 5, 10):
+            S = workloads.small_k(n=100, k=kk, knorm=knorm, seed=600 + kk)
+            A = (S["Q"] * S["lam"][None, :]) @ S["Q"].T + (S["K"] * S["sigma"].astype(float)[None, :]) @ S["K"].T
+            A = 0.5 * (A + A.T)
+            w = np.linalg.eigvalsh(A)
+            row = {"knorm": knorm, "k": kk}
+            for tag in ("method", "perturbation"):
+                Qs = torch.from_numpy(np.asfortranarray(S["Q"])).to(dev)
+                ls = torch.from_numpy(S["lam"].copy()).to(dev)
+                Ks = torch.from_numpy(np.asfortranarray(S["K"])).to(dev)
+                if tag == "method":
+                    eu.eig_update_rank_k(h, Qs, ls, Ks, S["sigma"], eu.EIG_VALUES | eu.EIG_VECTORS)
+                    m_, X_ = ls.cpu().numpy(), Qs.cpu().numpy()
+                else:
+                    mo = torch.empty(100, dtype=torch.float64, device=dev)
+                    Xo = torch.empty((100, 100), dtype=torch.float64, device=dev).t()
+                    eu.eig_perturbation(h, Qs, ls, Ks, S["sigma"], mo, Xo)
+                    m_, X_ = mo.cpu().numpy(), Xo.cpu().numpy()
+                row[tag] = {"A": float(np.linalg.norm(np.sort(m_) - w) / np.linalg.norm(w)),
+                            "B": float(np.linalg.norm(A - (X_ * m_[None, :]) @ X_.T, 2) / np.linalg.norm(A, 2)),
+                            "C": float(np.linalg.norm(X_.T @ X_ - np.eye(100), 2))}
+            panels.append(row)
+    out["figs_6_7_panels_n100"] = panels
+    # Fig. 4: one rank-2 update against two successive rank-1 updates, n = 4096
+    R = workloads.rank2_basic(seed=7, n=4096, k=2, device=dev, min_device_n=256)
+    Q0 = torch.from_numpy(np.asfortranarray(R["Q"])).to(dev)
+    l0 = torch.from_numpy(R["lam"].copy()).to(dev)
+    K2 = torch.from_numpy(np.asfortranarray(R["K"])).to(dev)
+    Qw, lw = Q0.clone(memory_format=torch.preserve_format), l0.clone()
+    want = eu.EIG_VALUES | eu.EIG_VECTORS
+
+    def one_rank2():
+        Qw.copy_(Q0)
+        lw.copy_(l0)
+        eu.eig_update_rank_k(h, Qw, lw, K2, None, want)
+
+    def two_rank1():
+        Qw.copy_(Q0)
+        lw.copy_(l0)
+        eu.eig_update_rank_k(h, Qw, lw, K2[:, 0:1], None, want)
+        eu.eig_update_rank_k(h, Qw, lw, K2[:, 1:2], None, want)
+
+    t2 = _time_ms(one_rank2, 3)
+    t11 = _time_ms(two_rank1, 3)
+    out["rank2_vs_two_rank1_n4096"] = {"rank2_ms": t2, "two_rank1_ms": t11, "ratio": t11 / t2}
+    eu.eig_update_destroy(h)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -461,6 +567,10 @@ def main():
         fp64 = {"value": R64["value"], "unit": UNIT, "ms_per_step": R64["ms"] / len(R64["reps"]),
                 "latency_ms": {"p50": R64["p50"], "p99": R64["p99"]}}
 
+    comparisons = None
+    if not args.no_comparisons and world == 1:
+        comparisons = run_comparisons(eu, dev, main_mode, P, R["ms"] / args.steps)
+
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(eu, dev, main_mode, max(1, min(args.steps, 3)))
@@ -511,6 +621,7 @@ def main():
             "gpu_launches": int(sum(r["launches"] for r in reps)),
             "batched": batched,
             "serving": serving,
+            "comparisons": comparisons,
             "roofline": dominant, "roofline_other": other, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P, args.cpu_sample)

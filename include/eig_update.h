@@ -95,7 +95,7 @@ typedef struct {
 typedef struct {
   int64_t n;            /* problem size */
   int64_t n_deflated;   /* pairs kept unchanged (|u_i| below the deflation bound) */
-  int64_t iters_total;  /* zero-finder evaluations summed over roots */
+  int64_t iters_total;  /* zero-finder FP64 evaluations summed over roots */
   int64_t n_notconv;    /* roots that hit the iteration cap */
   int32_t k;
   int32_t status;       /* final status of this update */
@@ -115,6 +115,10 @@ typedef struct {
   double ms_gemm;       /* X = Q W */
   int32_t launches;     /* kernels this update launched */
   int32_t pad_;
+  int64_t iters32_total; /* EIG_MIXED: coarse FP32 evaluations of the zero finder
+                            (iters_total counts the FP64 ones) */
+  int64_t redo32_total;  /* EIG_MIXED: FP32 evaluations whose root count the
+                            error bound could not certify (redone in FP64) */
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

@@ -360,6 +360,10 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     d.sidx = reinterpret_cast<int*>(b.take(sizeof(int) * ld * 2));
     d.mu_sec = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
     d.lam_old = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    if (mixed) {  // FP32 copies for the coarse phase of the zero finder
+      d.lamf = reinterpret_cast<float2*>(b.take(sizeof(float2) * ld));
+      d.Usf = reinterpret_cast<float*>(b.take(sizeof(float) * ld * K));
+    }
     if (vectors) {
       if (mixed) {
         d.Qs = reinterpret_cast<__nv_bfloat16*>(b.take(2 * (size_t)tc_num_slices() * tc_slice_plane((int)n)));
@@ -510,6 +514,8 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->status = status;
   rep->n_deflated = st.n_defl;
   rep->iters_total = st.iters_total;
+  rep->iters32_total = st.iters32_total;
+  rep->redo32_total = st.redo32_total;
   rep->iters_max = st.iters_max;
   rep->n_notconv = st.n_notconv;
   rep->norm_A = st.lam_absmax + st.fro2;

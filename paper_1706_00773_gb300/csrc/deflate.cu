@@ -76,7 +76,8 @@ __device__ __forceinline__ void deflate_body(
     int64_t n, int k, int K, const double* __restrict__ lam, const double* __restrict__ U,
     unsigned long long negmask, double* __restrict__ lam_keep, double* __restrict__ Us, int ld,
     int* __restrict__ idx_keep, int* __restrict__ idx_defl, double* __restrict__ lam_defl,
-    DevStatus* st, double* __restrict__ lam_old) {
+    DevStatus* st, double* __restrict__ lam_old, float2* __restrict__ lamf = nullptr,
+    float* __restrict__ Usf = nullptr) {
   __shared__ double shd[kDeflThreads];
   __shared__ int shi[kDeflThreads];
   __shared__ double colsq[EIG_MAX_K];
@@ -135,6 +136,12 @@ __device__ __forceinline__ void deflate_body(
       lam_keep[pk] = lam[i];
       idx_keep[pk] = (int)i;
       for (int c = 0; c < k; ++c) Us[(int64_t)c * ld + pk] = U[(int64_t)c * n + i];
+      if (lamf) {
+        // lam = hi + lo + O(2^-48 |lam|): the FP32 phase forms lam_i - lam_o from the pairs
+        const float hi = (float)lam[i];
+        lamf[pk] = make_float2(hi, (float)(lam[i] - (double)hi));
+        for (int c = 0; c < k; ++c) Usf[(int64_t)c * ld + pk] = (float)U[(int64_t)c * n + i];
+      }
       ++pk;
     } else {
       idx_defl[pd] = (int)i;
@@ -145,7 +152,10 @@ __device__ __forceinline__ void deflate_body(
   // Zero the tail rows and the padding columns the kernels may touch.
   for (int c = 0; c < K; ++c) {
     const int64_t from = (c < k) ? nkeep : 0;
-    for (int64_t i = from + t; i < ld; i += kDeflThreads) Us[(int64_t)c * ld + i] = 0.0;
+    for (int64_t i = from + t; i < ld; i += kDeflThreads) {
+      Us[(int64_t)c * ld + i] = 0.0;
+      if (Usf) Usf[(int64_t)c * ld + i] = 0.0f;
+    }
   }
   __syncthreads();
   if (t == 0) {
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
 __global__ void __launch_bounds__(kDeflThreads) deflate_grouped_kernel(const ProbDesc* __restrict__ P) {
   const ProbDesc& d = P[blockIdx.x];
   deflate_body(d.n, d.k, d.K, d.lam, d.U, d.negmask, d.lam_keep, d.Us, d.ld, d.idx_keep, d.idx_defl,
-               d.lam_defl, d.st, d.lam_old);
+               d.lam_defl, d.st, d.lam_old, d.lamf, d.Usf);
 }
 
 }  // namespace

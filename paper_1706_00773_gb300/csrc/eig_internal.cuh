@@ -39,12 +39,14 @@ struct DevStatus {
   int n_keep;
   int n_defl;
   int iters_max;
-  long long iters_total;
+  long long iters_total;   // FP64 evaluations of the zero finder
   long long n_notconv;
   double lam_absmax;
   double fro2;
   double lo_sent;
   double hi_sent;
+  long long iters32_total; // FP32 (coarse-phase) evaluations
+  long long redo32_total;  // FP32 evaluations whose count was not certified
 };
 
 // The non-deflated sub-problem in the layout the secular kernels read.  Its
@@ -60,6 +62,10 @@ struct Sub {
   const int* idx;     // n': original row index of kept row i
   const DevStatus* st;       // lo_sent / hi_sent: strict bounds on every root (Weyl)
   unsigned long long negmask;  // bit c set when sigma_c = -1
+  // FP32 copies for the coarse phase of the zero finder (null: FP64 only):
+  // lam' as (hi, lo) float pairs, U' as K float arrays of ld.
+  const float2* lamf = nullptr;
+  const float* Usf = nullptr;
 };
 
 // Per-root outputs of the zero finder.
@@ -155,6 +161,8 @@ struct ProbDesc {
   int* fcol;
   unsigned long long* rmax;
   DevStatus* st;
+  float2* lamf;            // mixed mode: FP32 copies for the coarse zero-finder phase
+  float* Usf;
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
@@ -168,6 +176,8 @@ __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
   s.idx = d.idx_keep;
   s.st = d.st;
   s.negmask = d.negmask;
+  s.lamf = d.lamf;
+  s.Usf = d.Usf;
   return s;
 }
 

@@ -181,6 +181,106 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
 }
 
 // ----------------------------------------------------------------------------
+// FP32 accumulation for the coarse phase of the zero finder (mixed mode).
+// The same sums as ACC_MN with x - lam_i formed from (hi, lo) float pairs as
+// (th - (hi_i - hi_o)) + (tl - (lo_i - lo_o)), tau = th + tl.  Measured from the
+// nearer bracketing pole (|tau| <= half the bracket), every other pole has
+// |x - lam_i| >= |lam_i - lam_o| / 2, so each term keeps ~2^-23 relative
+// accuracy; the pair representation adds an absolute error of 2^-48 |lam| per
+// difference.  Returns the two bound sums of the a-posteriori error of M^,
+//   S1 = sum_i |r_i| |u_i|^2   (relative rounding of the terms and the sums),
+//   S2 = sum_i r_i^2 |u_i|^2   (times the absolute error of x - lam_i),
+// through out2[0], out2[1] (lane 0 of every warp writes the same values).
+// ----------------------------------------------------------------------------
+template <int K, int E, int e>
+__device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, const float* __restrict__ Usf,
+                                             int ld, int n, float ho, float lo_o, float th, float tl,
+                                             int skip_a, int skip_b, double* sA, double* sB, double* out2,
+                                             int lane) {
+  constexpr int NS = nslots<K, E, e>();
+  constexpr int KP = K + 1;
+  float A[NS], B[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = 0.0f;
+    B[s] = 0.0f;
+  }
+  float s1 = 0.0f, s2 = 0.0f;
+  for (int i = lane; i < n; i += 32) {
+    const float2 l = __ldg(lamf + i);
+    const float d = (th - (l.x - ho)) + (tl - (l.y - lo_o));
+    float u[K];
+    float nu = 0.0f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      u[c] = __ldg(Usf + (size_t)c * ld + i);
+      nu = fmaf(u[c], u[c], nu);
+    }
+    const float r = (i == skip_a || i == skip_b) ? 0.0f : __frcp_rn(d);
+    s1 = fmaf(fabsf(r), nu, s1);
+    s2 = fmaf(r * r, nu, s2);
+    float t[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) t[c] = u[c] * r;
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (owner_of<K, E>(a) == e) {
+#pragma unroll
+        for (int b = a; b < K; ++b) {
+          A[s] = fmaf(t[a], u[b], A[s]);
+          B[s] = fmaf(t[a], t[b], B[s]);
+          ++s;
+        }
+      }
+    }
+  }
+  double A64[NS], B64[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A64[s] = warp_sum((double)A[s]);
+    B64[s] = warp_sum((double)B[s]);
+  }
+  const double S1 = warp_sum((double)s1), S2 = warp_sum((double)s2);
+  if (lane == 0) {
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (owner_of<K, E>(a) == e) {
+#pragma unroll
+        for (int b = a; b < K; ++b) {
+          sA[a * KP + b] = A64[s];
+          sA[b * KP + a] = A64[s];
+          sB[a * KP + b] = B64[s];
+          sB[b * KP + a] = B64[s];
+          ++s;
+        }
+      }
+    }
+    if (e == 0) {
+      out2[0] = S1;
+      out2[1] = S2;
+    }
+  }
+}
+
+template <int K, int E>
+__device__ __forceinline__ void accumulate32_group(int e, const float2* __restrict__ lamf,
+                                                   const float* __restrict__ Usf, int ld, int n, float ho,
+                                                   float lo_o, float th, float tl, int skip_a, int skip_b,
+                                                   double* sA, double* sB, double* out2, int lane) {
+  if (E == 1 || e == 0) {
+    accumulate32<K, E, 0>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+  } else if (E > 1 && e == 1) {
+    accumulate32<K, E, (E > 1 ? 1 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+  } else if (E > 2 && e == 2) {
+    accumulate32<K, E, (E > 2 ? 2 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+  } else {
+    accumulate32<K, E, (E > 3 ? 3 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Warp-parallel cyclic Jacobi on a symmetric K x K matrix in shared memory
 // (row stride K+1).  On exit the diagonal of A holds the eigenvalues and, if V
 // is given, V's columns the orthonormal eigenvectors.  Rotation (p,q) is the
@@ -444,8 +544,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
                                            int max_iter, const RootOut& out, DevStatus* st, int n,
                                            int m, double* sMg, double* sNg, double* sZg,
                                            double* sVg, double* s_tau, double* s_lamo,
-                                           int* s_done, int* s_ia, int* s_ib, int g, int e,
-                                           int lane) {
+                                           int* s_done, int* s_ia, int* s_ib, int* s_ph,
+                                           double* s_err, int g, int e, int lane) {
   constexpr int E = warps_per_root(K);
   constexpr int KP = K + 1;
   constexpr int Z2 = K + 2;
@@ -454,7 +554,10 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   const double* __restrict__ lam = sub.lam;
   const double* __restrict__ Us = sub.Us;
   // ---- placement (warp 0 of the group; every lane holds the same state) ----
-  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, slow = 0, ia = -1, ib = -1;
+  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, it32 = 0, slow = 0, ia = -1, ib = -1;
+  // Coarse phase in FP32 (mixed mode): steps from FP32 sums, the bracket moved
+  // only by counts that the error bound certifies; then FP64 to the end.
+  bool phase32 = (sub.lamf != nullptr);
   bool has_a = false, has_b = false, first = false, notconv = false;
   double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
   bool last_model = false;  // the current point came from a two-pole model step
@@ -496,6 +599,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       (*s_lamo) = lam[o];
       (*s_ia) = ia;
       (*s_ib) = ib;
+      (*s_ph) = phase32 ? 1 : 0;
     }
   }
   group_sync<E>(g);
@@ -503,8 +607,16 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   for (;;) {
     const double tau_c = (*s_tau);
     const double lam_o = (*s_lamo);
-    const int below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c,
-                                                     skip_a, skip_b, sMg, sNg, lane);
+    const bool ph32 = (*s_ph) != 0;
+    int below = 0;
+    if (ph32) {
+      const float ho = (float)lam_o, th32 = (float)tau_c;
+      accumulate32_group<K, E>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
+                               (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
+    } else {
+      below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b,
+                                             sMg, sNg, lane);
+    }
     group_sync<E>(g);
     if (e == 0) {
       const double* M = sMg;
@@ -585,8 +697,54 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       g12 = warp_sum(g12);
       g22 = warp_sum(g22);
       const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
+      // Inside the bracket #{lam_i < x} is the pole index p (FP32 sums leave it out).
+      if (ph32) below = has_a ? p : 0;
       const int count = below + __popc(posmask) - posD - sub.kplus;
+      // FP32 phase: the count is exact when no eigenvalue of Z can change sign
+      // under the error of the FP32 sums, which only enters the K x K block:
+      //   E = |dM^|_2 <= (L + 8) 2^-24 S1 + 2^-46 max|lam| S2   (L terms per lane),
+      // plus the Jacobi's own rounding.  Eigenvalues with |z_j| > 2E keep their
+      // sign (Weyl).  The small ones belong to eigenvectors that live almost
+      // entirely in the two bordered rows; with s the small set, W = |V_{K,s}|_F^2
+      // (their weight in the K block) and g the distance of the large ones from
+      // zero, each small eigenvalue moves by at most E W + E^2 W / g (a
+      // Hermitian block perturbation with the large block eliminated).  If any
+      // sign is not certain this point is evaluated again in FP64 and the FP64
+      // phase takes over.
+      bool redo = false, conv = false;
+      if (ph32) {
+        const bool nonfin = __any_sync(0xffffffffu, lane < Z2 && !isfinite(zj));
+        double zmax = (lane < Z2) ? fabs(zj) : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
+        const double L = (double)((n + 31) / 32);
+        const double E = 1.25 * ((L + 8.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
+                         64.0 * kEps * zmax;
+        const bool small = lane < Z2 && !(fabs(zj) > 2.0 * E);
+        double wk = 0.0;
+        if (small) {
+          for (int c = 0; c < K; ++c) wk = fma(V[c * ZP + lane], V[c * ZP + lane], wk);
+        }
+        double zs = small ? fabs(zj) : INFINITY;
+        double zb = (lane < Z2 && !small) ? fabs(zj) : INFINITY;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          wk += __shfl_xor_sync(0xffffffffu, wk, off);
+          zs = fmin(zs, __shfl_xor_sync(0xffffffffu, zs, off));
+          zb = fmin(zb, __shfl_xor_sync(0xffffffffu, zb, off));
+        }
+        const double g = zb - E;
+        const double shift = E * wk + E * E * wk / g;
+        const bool any_small = zs < INFINITY;
+        redo = nonfin || !(E < INFINITY) ||
+               (any_small && !(g > 0.0 && zs > 2.0 * shift + 64.0 * kEps * zmax));
+      }
+      if (redo) {
+        phase32 = false;
+        if (lane == 0) atomicAdd((unsigned long long*)&st->redo32_total, 1ull);
+      } else {
       ++it;
+      if (ph32) ++it32;
       const double wprev = th - tl;
       if (count <= m) {
         tl = tau;
@@ -642,7 +800,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           }
         }
       }
-      bool conv = false, newton = false;
+      bool newton = false;
       double tn = tau;
       const int inb = c_hi - c_lo;  // roots in the bracket
       const int r_in = m - c_lo;    // our root's rank among them
@@ -654,7 +812,11 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       if (inb == 1) {
         const double step = -1.0 / tsum;
         tn = tau + step;
-        if (step == 0.0) {
+        // A step below half an ulp of tau leaves tau where it is.  tau is the
+        // bracket end the count just moved; if the step points into the bracket
+        // the root is within rounding of tau (an outward step means another
+        // root sits just outside: keep bisecting).
+        if (step == 0.0 || (tn == tau && ((tau == tl && step > 0.0) || (tau == th && step < 0.0)))) {
           conv = true;
           tn = tau;
         } else if (it <= 2 && isfinite(model)) {
@@ -696,6 +858,23 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       if (!conv && it >= max_iter) {
         conv = true;
         notconv = true;
+      }
+      if (ph32) {
+        // A root is never finished on FP32 sums; near FP32 resolution (a small
+        // Newton step or bracket) the FP64 phase takes over at the next point.
+        if (conv) {
+          conv = false;
+          notconv = false;
+          phase32 = false;
+        } else if ((newton && fabs(tn - tau) <= 1e-5 * fabs(tn)) || it32 >= 16 ||
+                   (th - tl) <= 1e-5 * fmax(fabs(tl), fabs(th))) {
+          phase32 = false;
+        }
+        if (!phase32) {
+          prev_step = INFINITY;
+          slow = 0;
+          last_model = false;
+        }
       }
       const double delta = tn - tau;  // the accepted point minus the evaluated one
       tau = tn;
@@ -749,7 +928,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           out.tau[m] = tau;
           out.iters[m] = it;
           out.flags[m] = notconv ? 1 : 0;
-          atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)it);
+          atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)(it - it32));
+          if (it32) atomicAdd((unsigned long long*)&st->iters32_total, (unsigned long long)it32);
           atomicMax(&st->iters_max, it);
           if (notconv) {
             atomicAdd((unsigned long long*)&st->n_notconv, 1ull);
@@ -757,10 +937,12 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           }
         }
       }
+      }  // !redo
       if (lane == 0) {
         (*s_tau) = tau;
         (*s_lamo) = lam[o];
         (*s_done) = conv ? 1 : 0;
+        (*s_ph) = phase32 ? 1 : 0;
       }
     }
     group_sync<E>(g);
@@ -779,7 +961,8 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   constexpr int ZP = K + 3;
   __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
-  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G];
+  __shared__ double s_err[G][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
@@ -791,7 +974,7 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
     const int m = s_m[g];
     if (m >= stop) break;
     root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
-                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], g, e, lane);
+                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], g, e, lane);
   }
 }
 
@@ -806,7 +989,8 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
   constexpr int ZP = K + 3;
   __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
-  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G];
+  __shared__ double s_err[G][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   const int total = c.pk[c.count];
@@ -821,7 +1005,7 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
     const Sub sub = sub_of(d);
     root_solve<K>(sub, d.pole_cnt, max_iter, rootout_of(d), d.st, *sub.n_dev, item - c.pk[p],
                   sM[g], sN[g], sZ[g], sV[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
-                  &s_ib[g], g, e, lane);
+                  &s_ib[g], &s_ph[g], s_err[g], g, e, lane);
   }
 }
 

@@ -281,8 +281,12 @@ def test_mixed_matches_fp64_and_oracle(eu, handle, handle_mixed, n, k, sigma):
     assert rc == 0
     rc, rep, mum, Xm = _run_update(eu, handle_mixed, P)
     assert rc == 0 and rep["status"] == 0
-    # the secular stage is the same FP64 path in both modes
-    assert np.array_equal(mum, mu64)
+    # Mixed mode runs the zero finder's coarse steps on FP32 sums (bracket moved
+    # only by certified counts) and finishes every root in FP64: the roots agree
+    # with the FP64 mode's to rounding.
+    assert np.max(np.abs(mum - mu64)) <= 1e-13 * norm2_A(P["lam"], P["K"])
+    if n > 1:
+        assert rep["iters32_total"] > 0
     # X from the tensor cores vs the FP64 GEMM: 5 slices keep ~2^-40 of the scale
     assert np.max(np.abs(Xm - X64)) <= 1e-10
     _check_full(P, mum, Xm)
