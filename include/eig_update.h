@@ -119,6 +119,9 @@ typedef struct {
                             (iters_total counts the FP64 ones) */
   int64_t redo32_total;  /* EIG_MIXED: FP32 evaluations whose root count the
                             error bound could not certify (redone in FP64) */
+  int64_t taylor_total;  /* evaluations taken by a first-order update of the
+                            k x k sums after a tiny Newton step (no pass over
+                            the terms) */
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

@@ -72,7 +72,7 @@ class eig_report(ctypes.Structure):
                 ("ms_counts", ctypes.c_double), ("ms_roots", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_slice", ctypes.c_double), ("ms_gemm", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("pad_", ctypes.c_int32), ("iters32_total", ctypes.c_int64),
-                ("redo32_total", ctypes.c_int64)]
+                ("redo32_total", ctypes.c_int64), ("taylor_total", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

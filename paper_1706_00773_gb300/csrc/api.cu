@@ -516,6 +516,7 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->iters_total = st.iters_total;
   rep->iters32_total = st.iters32_total;
   rep->redo32_total = st.redo32_total;
+  rep->taylor_total = st.taylor_total;
   rep->iters_max = st.iters_max;
   rep->n_notconv = st.n_notconv;
   rep->norm_A = st.lam_absmax + st.fro2;

@@ -47,6 +47,8 @@ struct DevStatus {
   double hi_sent;
   long long iters32_total; // FP32 (coarse-phase) evaluations
   long long redo32_total;  // FP32 evaluations whose count was not certified
+  long long taylor_total;  // evaluations by a first-order update of the K x K sums
+  long long pad_;
 };
 
 // The non-deflated sub-problem in the layout the secular kernels read.  Its

@@ -281,10 +281,21 @@ __device__ __forceinline__ void accumulate32_group(int e, const float2* __restri
 }
 
 // ----------------------------------------------------------------------------
-// Warp-parallel cyclic Jacobi on a symmetric K x K matrix in shared memory
-// (row stride K+1).  On exit the diagonal of A holds the eigenvalues and, if V
-// is given, V's columns the orthonormal eigenvectors.  Rotation (p,q) is the
-// symmetric 2x2 Schur decomposition; lane r applies it to row/column r.
+// Warp-parallel Jacobi on a symmetric K x K matrix in shared memory (row
+// stride K+1).  On exit the diagonal of A holds the eigenvalues and, if V is
+// given, V's columns the orthonormal eigenvectors (accumulated onto V when
+// init_v is false).
+//
+// Round-robin (parallel) ordering: each round rotates ceil(K/2) disjoint index
+// pairs at once, one lane per pair computing its angle, then every lane applies
+// the rotations to its share of columns, rows and V.  The angle is taken in
+// FP32 (t = tan of the rotation): any angle near the annihilating one gives an
+// exactly orthogonal rotation when c and s are formed from t in FP64, here
+// c = 1/sqrt(1 + t^2) by two Newton steps of the inverse-square-root iteration
+// y <- y (3 - x y^2)/2 from an FP32 start, s = t c.  The rotated matrix is
+// formed by the rotation itself (no diagonal shortcut), so A stays an exact
+// similarity of the input up to rounding; the off-diagonal residual an
+// inexact angle leaves is removed by later rounds.
 // ----------------------------------------------------------------------------
 template <int K>
 __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) {
@@ -297,6 +308,9 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
   }
   __syncwarp();
   if constexpr (K == 1) return;
+  constexpr int M = (K + 1) / 2 * 2;  // even number of players (K odd: one idle)
+  constexpr int P = M / 2;            // pairs per round
+  constexpr int ITEMS = P * K;        // (pair, row) updates per pass
   for (int sweep = 0; sweep < 16; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int idx = lane; idx < K * K; idx += 32) {
@@ -307,56 +321,89 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
     off = warp_sum(off);
     dia = warp_sum(dia);
     if (off == 0.0 || off <= 1e-36 * dia) break;
-    for (int p = 0; p < K - 1; ++p) {
-      for (int q = p + 1; q < K; ++q) {
-        const double apq = A[p * KP + q];
-        const double app = A[p * KP + p];
-        const double aqq = A[q * KP + q];
-        __syncwarp();
-        if (apq == 0.0) continue;
-        if (sweep > 2 && fabs(apq) * 1e18 < fabs(app) && fabs(apq) * 1e18 < fabs(aqq)) {
-          if (lane == 0) {
-            A[p * KP + q] = 0.0;
-            A[q * KP + p] = 0.0;
-          }
-          __syncwarp();
-          continue;
-        }
-        const double theta = (aqq - app) / (2.0 * apq);
-        double t;
-        if (fabs(theta) > 1e150) {
-          t = 0.5 / theta;
-        } else {
-          t = 1.0 / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-          if (theta < 0.0) t = -t;
-        }
-        const double c = 1.0 / sqrt(fma(t, t, 1.0));
-        const double s = t * c;
-        if (lane < K) {
-          const double arp = A[lane * KP + p], arq = A[lane * KP + q];
-          A[lane * KP + p] = c * arp - s * arq;
-          A[lane * KP + q] = s * arp + c * arq;
-        }
-        __syncwarp();
-        if (lane < K) {
-          const double apr = A[p * KP + lane], aqr = A[q * KP + lane];
-          A[p * KP + lane] = c * apr - s * aqr;
-          A[q * KP + lane] = s * apr + c * aqr;
-        }
-        __syncwarp();
+    for (int rnd = 0; rnd < M - 1; ++rnd) {
+      int pj = 0, qj = 0;
+      double cj = 1.0, sj = 0.0;
+      bool act = false;
+      if (lane < P) {
+        int a, b;
         if (lane == 0) {
-          A[p * KP + p] = app - t * apq;
-          A[q * KP + q] = aqq + t * apq;
-          A[p * KP + q] = 0.0;
-          A[q * KP + p] = 0.0;
+          a = rnd;
+          b = M - 1;
+        } else {
+          a = (rnd + lane) % (M - 1);
+          b = (rnd - lane + (M - 1)) % (M - 1);
         }
-        if (V && lane < K) {
-          const double vrp = V[lane * KP + p], vrq = V[lane * KP + q];
-          V[lane * KP + p] = c * vrp - s * vrq;
-          V[lane * KP + q] = s * vrp + c * vrq;
+        pj = a < b ? a : b;
+        qj = a < b ? b : a;
+        if (qj < K) {
+          const double apq = A[pj * KP + qj], app = A[pj * KP + pj], aqq = A[qj * KP + qj];
+          if (apq != 0.0) {
+            if (sweep > 2 && fabs(apq) * 1e18 < fabs(app) && fabs(apq) * 1e18 < fabs(aqq)) {
+              A[pj * KP + qj] = 0.0;  // negligible against both diagonal entries
+              A[qj * KP + pj] = 0.0;
+            } else {
+              const float fa = (float)apq;
+              if (fa != 0.0f) {
+                const float th = (float)(aqq - app) / (2.0f * fa);
+                float t;
+                if (!(fabsf(th) <= 1e18f)) {
+                  t = 0.5f / th;  // also th = +-inf: t = 0
+                } else {
+                  t = 1.0f / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+                  if (th < 0.0f) t = -t;
+                }
+                const double td = (double)t;
+                const double x = fma(td, td, 1.0);
+                double y = (double)rsqrtf((float)x);
+                y = y * fma(-0.5 * x * y, y, 1.5);
+                y = y * fma(-0.5 * x * y, y, 1.5);
+                cj = y;
+                sj = td * y;
+                act = true;
+              }
+            }
+          }
         }
-        __syncwarp();
       }
+      __syncwarp();
+      // columns: A <- A J
+#pragma unroll
+      for (int base = 0; base < ITEMS; base += 32) {
+        const int idx = base + lane;
+        const int jj = idx < ITEMS ? idx / K : 0;
+        const int r = idx - jj * K;
+        const int p = __shfl_sync(0xffffffffu, pj, jj), q = __shfl_sync(0xffffffffu, qj, jj);
+        const double c = __shfl_sync(0xffffffffu, cj, jj), sn = __shfl_sync(0xffffffffu, sj, jj);
+        const bool go = __shfl_sync(0xffffffffu, act ? 1 : 0, jj) != 0;
+        if (idx < ITEMS && go) {
+          const double arp = A[r * KP + p], arq = A[r * KP + q];
+          A[r * KP + p] = c * arp - sn * arq;
+          A[r * KP + q] = sn * arp + c * arq;
+        }
+      }
+      __syncwarp();
+      // rows: A <- J^T A, and V <- V J
+#pragma unroll
+      for (int base = 0; base < ITEMS; base += 32) {
+        const int idx = base + lane;
+        const int jj = idx < ITEMS ? idx / K : 0;
+        const int r = idx - jj * K;
+        const int p = __shfl_sync(0xffffffffu, pj, jj), q = __shfl_sync(0xffffffffu, qj, jj);
+        const double c = __shfl_sync(0xffffffffu, cj, jj), sn = __shfl_sync(0xffffffffu, sj, jj);
+        const bool go = __shfl_sync(0xffffffffu, act ? 1 : 0, jj) != 0;
+        if (idx < ITEMS && go) {
+          const double apr = A[p * KP + r], aqr = A[q * KP + r];
+          A[p * KP + r] = c * apr - sn * aqr;
+          A[q * KP + r] = sn * apr + c * aqr;
+          if (V) {
+            const double vrp = V[r * KP + p], vrq = V[r * KP + q];
+            V[r * KP + p] = c * vrp - sn * vrq;
+            V[r * KP + q] = sn * vrp + c * vrq;
+          }
+        }
+      }
+      __syncwarp();
     }
   }
 }
@@ -545,7 +592,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
                                            int m, double* sMg, double* sNg, double* sZg,
                                            double* sVg, double* s_tau, double* s_lamo,
                                            int* s_done, int* s_ia, int* s_ib, int* s_ph,
-                                           double* s_err, int g, int e, int lane) {
+                                           double* s_err, int* s_tay, double* s_step, int g, int e,
+                                           int lane) {
   constexpr int E = warps_per_root(K);
   constexpr int KP = K + 1;
   constexpr int Z2 = K + 2;
@@ -554,7 +602,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   const double* __restrict__ lam = sub.lam;
   const double* __restrict__ Us = sub.Us;
   // ---- placement (warp 0 of the group; every lane holds the same state) ----
-  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, it32 = 0, slow = 0, ia = -1, ib = -1;
+  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, it32 = 0, itay = 0, slow = 0, ia = -1, ib = -1;
   // Coarse phase in FP32 (mixed mode): steps from FP32 sums, the bracket moved
   // only by counts that the error bound certifies; then FP64 to the end.
   bool phase32 = (sub.lamf != nullptr);
@@ -600,6 +648,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       (*s_ia) = ia;
       (*s_ib) = ib;
       (*s_ph) = phase32 ? 1 : 0;
+      (*s_tay) = 0;
     }
   }
   group_sync<E>(g);
@@ -608,8 +657,22 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
     const double tau_c = (*s_tau);
     const double lam_o = (*s_lamo);
     const bool ph32 = (*s_ph) != 0;
+    // After a small Newton step (|s| <= 1e-8 of the distance to every pole in
+    // the sums) the sums move to first order: M^(x+s) = M^(x) - s N^(x), with
+    // an error below s^2 tr(N^)/d_min <= 1e-16 of their own scale, and N^ is
+    // kept.  No pass over the terms.
+    const bool tay = (*s_tay) != 0;
     int below = 0;
-    if (ph32) {
+    if (tay) {
+      if (e == 0) {
+        const double sstep = (*s_step);
+        for (int idx = lane; idx < K * K; idx += 32) {
+          const int r = idx / K, c = idx - (idx / K) * K;
+          sMg[r * KP + c] = fma(-sstep, sNg[r * KP + c], sMg[r * KP + c]);
+        }
+        __syncwarp();
+      }
+    } else if (ph32) {
       const float ho = (float)lam_o, th32 = (float)tau_c;
       accumulate32_group<K, E>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
                                (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
@@ -697,8 +760,9 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       g12 = warp_sum(g12);
       g22 = warp_sum(g22);
       const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
-      // Inside the bracket #{lam_i < x} is the pole index p (FP32 sums leave it out).
-      if (ph32) below = has_a ? p : 0;
+      // Inside the bracket #{lam_i < x} is the pole index p (FP32 sums and
+      // first-order updates leave it out).
+      if (ph32 || tay) below = has_a ? p : 0;
       const int count = below + __popc(posmask) - posD - sub.kplus;
       // FP32 phase: the count is exact when no eigenvalue of Z can change sign
       // under the error of the FP32 sums, which only enters the K x K block:
@@ -740,11 +804,24 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
                (any_small && !(g > 0.0 && zs > 2.0 * shift + 64.0 * kEps * zmax));
       }
       if (redo) {
+        // The count is uncertain but the FP32 Newton step is still good: with
+        // one root in the bracket and the step inside it, the FP64 phase
+        // starts at the stepped point (the bracket is left as it was).
         phase32 = false;
+        prev_step = INFINITY;
+        slow = 0;
+        last_model = false;
         if (lane == 0) atomicAdd((unsigned long long*)&st->redo32_total, 1ull);
+        const double tn0 = tau - 1.0 / tsum;
+        if (c_hi - c_lo == 1 && isfinite(tn0) && tn0 > tl && tn0 < th) {
+          tau = tn0;
+          ++it;
+          ++it32;
+        }
       } else {
       ++it;
       if (ph32) ++it32;
+      if (tay) ++itay;
       const double wprev = th - tl;
       if (count <= m) {
         tl = tau;
@@ -877,6 +954,17 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
         }
       }
       const double delta = tn - tau;  // the accepted point minus the evaluated one
+      // Next evaluation by the first-order update when the Newton step is tiny
+      // against the nearest pole inside the sums (the neighbours of the bracket).
+      bool tay_next = false;
+      if (!ph32 && !phase32 && newton && !conv) {
+        double dmin = INFINITY;
+        const int lo_nb = (ia >= 1) ? ia - 1 : -1;
+        const int hi_nb = (ib >= 0 && ib + 1 < n) ? ib + 1 : -1;
+        if (lo_nb >= 0) dmin = fmin(dmin, fabs(tau - (lam[lo_nb] - lam[o])));
+        if (hi_nb >= 0) dmin = fmin(dmin, fabs(tau - (lam[hi_nb] - lam[o])));
+        tay_next = fabs(delta) <= 1e-8 * dmin;
+      }
       tau = tn;
       if (conv) {
         // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
@@ -928,7 +1016,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           out.tau[m] = tau;
           out.iters[m] = it;
           out.flags[m] = notconv ? 1 : 0;
-          atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)(it - it32));
+          atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)(it - it32 - itay));
+          if (itay) atomicAdd((unsigned long long*)&st->taylor_total, (unsigned long long)itay);
           if (it32) atomicAdd((unsigned long long*)&st->iters32_total, (unsigned long long)it32);
           atomicMax(&st->iters_max, it);
           if (notconv) {
@@ -937,12 +1026,17 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           }
         }
       }
+        if (lane == 0) {
+          (*s_tay) = tay_next ? 1 : 0;
+          (*s_step) = delta;
+        }
       }  // !redo
       if (lane == 0) {
         (*s_tau) = tau;
         (*s_lamo) = lam[o];
         (*s_done) = conv ? 1 : 0;
         (*s_ph) = phase32 ? 1 : 0;
+        if (redo) (*s_tay) = 0;
       }
     }
     group_sync<E>(g);
@@ -961,8 +1055,8 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   constexpr int ZP = K + 3;
   __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
-  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G];
-  __shared__ double s_err[G][2];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
+  __shared__ double s_err[G][2], s_step[G];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
@@ -974,7 +1068,7 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
     const int m = s_m[g];
     if (m >= stop) break;
     root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
-                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], g, e, lane);
+                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }
 
@@ -989,8 +1083,8 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
   constexpr int ZP = K + 3;
   __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
-  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G];
-  __shared__ double s_err[G][2];
+  __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
+  __shared__ double s_err[G][2], s_step[G];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   const int total = c.pk[c.count];
@@ -1005,7 +1099,7 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
     const Sub sub = sub_of(d);
     root_solve<K>(sub, d.pole_cnt, max_iter, rootout_of(d), d.st, *sub.n_dev, item - c.pk[p],
                   sM[g], sN[g], sZ[g], sV[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
-                  &s_ib[g], &s_ph[g], s_err[g], g, e, lane);
+                  &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }
 
