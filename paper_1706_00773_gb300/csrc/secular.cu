@@ -192,7 +192,7 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
 //   S2 = sum_i r_i^2 |u_i|^2   (times the absolute error of x - lam_i),
 // through out2[0], out2[1] (lane 0 of every warp writes the same values).
 // ----------------------------------------------------------------------------
-template <int K, int E, int e>
+template <int K, int E, int e, bool WN>
 __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, const float* __restrict__ Usf,
                                              int ld, int n, float ho, float lo_o, float th, float tl,
                                              int skip_a, int skip_b, double* sA, double* sB, double* out2,
@@ -229,7 +229,7 @@ __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, co
 #pragma unroll
         for (int b = a; b < K; ++b) {
           A[s] = fmaf(t[a], u[b], A[s]);
-          B[s] = fmaf(t[a], t[b], B[s]);
+          if (WN) B[s] = fmaf(t[a], t[b], B[s]);
           ++s;
         }
       }
@@ -239,7 +239,7 @@ __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, co
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     A64[s] = warp_sum((double)A[s]);
-    B64[s] = warp_sum((double)B[s]);
+    B64[s] = WN ? warp_sum((double)B[s]) : 0.0;
   }
   const double S1 = warp_sum((double)s1), S2 = warp_sum((double)s2);
   if (lane == 0) {
@@ -251,8 +251,10 @@ __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, co
         for (int b = a; b < K; ++b) {
           sA[a * KP + b] = A64[s];
           sA[b * KP + a] = A64[s];
-          sB[a * KP + b] = B64[s];
-          sB[b * KP + a] = B64[s];
+          if (WN) {
+            sB[a * KP + b] = B64[s];
+            sB[b * KP + a] = B64[s];
+          }
           ++s;
         }
       }
@@ -264,19 +266,22 @@ __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, co
   }
 }
 
-template <int K, int E>
+template <int K, int E, bool WN>
 __device__ __forceinline__ void accumulate32_group(int e, const float2* __restrict__ lamf,
                                                    const float* __restrict__ Usf, int ld, int n, float ho,
                                                    float lo_o, float th, float tl, int skip_a, int skip_b,
                                                    double* sA, double* sB, double* out2, int lane) {
   if (E == 1 || e == 0) {
-    accumulate32<K, E, 0>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+    accumulate32<K, E, 0, WN>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
   } else if (E > 1 && e == 1) {
-    accumulate32<K, E, (E > 1 ? 1 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+    accumulate32<K, E, (E > 1 ? 1 : 0), WN>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2,
+                                            lane);
   } else if (E > 2 && e == 2) {
-    accumulate32<K, E, (E > 2 ? 2 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+    accumulate32<K, E, (E > 2 ? 2 : 0), WN>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2,
+                                            lane);
   } else {
-    accumulate32<K, E, (E > 3 ? 3 : 0)>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2, lane);
+    accumulate32<K, E, (E > 3 ? 3 : 0), WN>(lamf, Usf, ld, n, ho, lo_o, th, tl, skip_a, skip_b, sA, sB, out2,
+                                            lane);
   }
 }
 
@@ -425,23 +430,48 @@ __device__ __forceinline__ double sigma_of(unsigned long long negmask, int a) {
 // ----------------------------------------------------------------------------
 template <int K>
 __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, bool absolute,
-                                            double tau, double lam_o, int* out, double* M,
-                                            double* Gm, double* Vg, double* Ev, int g, int e,
-                                            int lane) {
+                                            double tau, double lam_o, int pole, int* out, double* M0,
+                                            double* Gm, double* Vg, double* Ev, double* s_err, int* s_redo,
+                                            int g, int e, int lane) {
   constexpr int E = warps_per_root(K);
   constexpr int KP = K + 1;
-  int below = 0;
-  if (active)
-    below = accumulate_group<K, E, ACC_MG>(e, sub.lam, sub.Us, sub.ld, n, lam_o, absolute, tau,
-                                           -1, -1, M, Gm, lane);
+  // At a pole with FP32 copies present, a first pass sums M~ in FP32 (the
+  // pole's own term u_q u_q^T exactly in FP64 as G, #{lam_i < lam_q} = q);
+  // a count that the error bound cannot certify is taken again in FP64.  A
+  // repeated or nearly repeated pole gives 1/0 in FP32, an infinite bound,
+  // and so the FP64 pass.
+  const bool try32 = !absolute && sub.lamf != nullptr;
+  for (int pass = try32 ? 0 : 1; pass < 2; ++pass) {
+    const bool p32 = (pass == 0);
+    double* M = M0;
+    int below = 0;
+    if (active) {
+      if (p32) {
+        const float ho = (float)lam_o;
+        accumulate32_group<K, E, false>(e, sub.lamf, sub.Usf, sub.ld, n, ho, (float)(lam_o - (double)ho), 0.0f,
+                                        0.0f, pole, -1, M, Gm, s_err, lane);
+      } else {
+        below = accumulate_group<K, E, ACC_MG>(e, sub.lam, sub.Us, sub.ld, n, lam_o, absolute, tau, -1, -1, M,
+                                               Gm, lane);
+      }
+    }
     group_sync<E>(g);
     if (active && e == 0) {
+      if (p32) {
+        below = pole;
+        for (int idx = lane; idx < K * K; idx += 32) {
+          const int r = idx / K, c = idx - (idx / K) * K;
+          Gm[r * KP + c] = sub.Us[(size_t)r * sub.ld + pole] * sub.Us[(size_t)c * sub.ld + pole];
+        }
+        __syncwarp();
+      }
       for (int idx = lane; idx < K * K; idx += 32) {
         const int r = idx / K, c = idx - (idx / K) * K;
         const double v = -M[r * KP + c];
         M[r * KP + c] = (r == c) ? v + sigma_of(sub.negmask, r) : v;
       }
       double gmax = 0.0;
+      double tol_rng = INFINITY;
       for (int idx = lane; idx < K * K; idx += 32) {
         const int r = idx / K, c = idx - (idx / K) * K;
         gmax = fmax(gmax, fabs(Gm[r * KP + c]));
@@ -459,6 +489,7 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
         double emax = 0.0;
         for (int j = 0; j < K; ++j) emax = fmax(emax, Ev[j]);
         const double tol = 64.0 * kEps * K * emax;
+        tol_rng = tol;
         for (int j = 0; j < K; ++j) dimR += (Ev[j] > tol) ? 1 : 0;
         // T = V^T B V into Gm: lane j forms column j.
         double bv[K];
@@ -497,10 +528,30 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
       }
       const unsigned pos = __ballot_sync(0xffffffffu, lane < K && M[(lane < K ? lane : 0) * KP + (lane < K ? lane : 0)] > 0.0);
       const int cnt = below + dimR + __popc(pos) - sub.kplus;
-      if (lane == 0) *out = cnt;
+      bool ok = true;
+      if (p32) {
+        // Certify: each eigenvalue on R^perp must clear the FP32 error of M~
+        // (Weyl; V is orthogonal), E = (L + 8) 2^-24 S1 + 2^-46 max|lam| S2.
+        const bool rng = lane < K && gmax > 0.0 && Ev[lane] > tol_rng;
+        const double v = (lane < K) ? M[lane * KP + lane] : 0.0;
+        double vmax = (lane < K && !rng) ? fabs(v) : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+        const double L = (double)((n + 31) / 32);
+        const double Eb = 1.25 * ((L + 8.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
+                          64.0 * kEps * vmax;
+        const bool okj = lane >= K || rng || fabs(v) > 2.0 * Eb;
+        ok = __all_sync(0xffffffffu, okj) && (Eb < INFINITY) && isfinite(vmax);
+      }
+      if (lane == 0) {
+        if (ok) *out = cnt;
+        *s_redo = ok ? 0 : 1;
+      }
       __syncwarp();
-    }
+        }
     group_sync<E>(g);
+    if (!p32 || !active || (*s_redo) == 0) break;
+  }
 }
 
 template <int K>
@@ -511,7 +562,8 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
   constexpr int G = 4 / E;
   constexpr int KP = K + 1;
   __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
-  __shared__ double sEv[G][K];
+  __shared__ double sEv[G][K], s_err[G][2];
+  __shared__ int s_redo[G];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
@@ -526,8 +578,8 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
     const bool active = pt < limit;
     const double tau = (active && absolute) ? xs[pt] : 0.0;
     const double lam_o = (active && !absolute) ? sub.lam[pt] : 0.0;
-    count_point<K>(sub, n, active, absolute, tau, lam_o, active ? counts + pt : nullptr, sM[g],
-                   sG[g], sV[g], sEv[g], g, e, lane);
+    count_point<K>(sub, n, active, absolute, tau, lam_o, pt, active ? counts + pt : nullptr, sM[g],
+                   sG[g], sV[g], sEv[g], s_err[g], &s_redo[g], g, e, lane);
   }
 }
 
@@ -539,7 +591,8 @@ __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __r
   constexpr int G = 4 / E;
   constexpr int KP = K + 1;
   __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
-  __shared__ double sEv[G][K];
+  __shared__ double sEv[G][K], s_err[G][2];
+  __shared__ int s_redo[G];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   const int total = c.pk[c.count];
@@ -563,7 +616,8 @@ __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __r
         out = d.pole_cnt + pt;
       }
     }
-    count_point<K>(sub, n, active, false, 0.0, lam_o, out, sM[g], sG[g], sV[g], sEv[g], g, e, lane);
+    count_point<K>(sub, n, active, false, 0.0, lam_o, pt, out, sM[g], sG[g], sV[g], sEv[g], s_err[g], &s_redo[g],
+                   g, e, lane);
   }
 }
 
@@ -674,7 +728,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       }
     } else if (ph32) {
       const float ho = (float)lam_o, th32 = (float)tau_c;
-      accumulate32_group<K, E>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
+      accumulate32_group<K, E, true>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
                                (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
     } else {
       below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b,
@@ -706,24 +760,43 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       __syncwarp();
       if (it > 0) {
         // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
-        // then let Jacobi finish and accumulate onto V.
-        double zv[Z2];
-        if (lane < Z2) {
+        // then let Jacobi finish and accumulate onto V.  T = Z V, then V^T T,
+        // each entry by one lane (all 32 lanes busy), T kept in Z's storage.
+        constexpr int ZE = Z2 * Z2;
+        constexpr int NB = (ZE + 31) / 32;
+        double tv[NB];
 #pragma unroll
-          for (int r = 0; r < Z2; ++r) {
-            double acc = 0.0;
-            for (int c = 0; c < Z2; ++c) acc = fma(Z[r * ZP + c], V[c * ZP + lane], acc);
-            zv[r] = acc;
+        for (int b = 0; b < NB; ++b) {
+          const int idx = b * 32 + lane;
+          double acc = 0.0;
+          if (idx < ZE) {
+            const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
+            for (int q = 0; q < Z2; ++q) acc = fma(Z[r * ZP + q], V[q * ZP + c], acc);
           }
+          tv[b] = acc;
         }
         __syncwarp();
-        if (lane < Z2) {
-          for (int i = 0; i < Z2; ++i) {
-            double acc = 0.0;
 #pragma unroll
-            for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], zv[r], acc);
-            Z[i * ZP + lane] = acc;
+        for (int b = 0; b < NB; ++b) {
+          const int idx = b * 32 + lane;
+          if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int idx = b * 32 + lane;
+          double acc = 0.0;
+          if (idx < ZE) {
+            const int i = idx / Z2, c = idx - (idx / Z2) * Z2;
+            for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], Z[r * ZP + c], acc);
           }
+          tv[b] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int idx = b * 32 + lane;
+          if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
         }
         __syncwarp();
         if (lane < Z2) {  // exact symmetry
