@@ -1224,6 +1224,7 @@ __global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_
 }
 
 constexpr int kAsmThreads = 256;
+constexpr int kAsmCache = 32;
 
 // One CTA per secular root m: w_i = (u_i^T alpha) / (lam_i - mu), |w| = 1, the
 // entry of largest magnitude made positive, scattered to W[idx_i, pos].
@@ -1257,14 +1258,32 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
     for (int c = 0; c < K; ++c) ua = fma(sub.Us[(size_t)c * sub.ld + i], al[c], ua);
     return ua / ((sub.lam[i] - lam_o) - tau);
   };
+  // Up to kAsmCache entries per thread are kept in registers for the writing
+  // pass (n' <= kAsmThreads * kAsmCache); larger columns are recomputed.
+  const bool cached = nk <= kAsmThreads * kAsmCache;
+  double wc[kAsmCache];
   double n2 = 0.0, mx = -1.0;
   int ix = 0x7fffffff;
-  for (int i = t; i < nk; i += kAsmThreads) {
-    const double w = wcomp(i);
-    n2 = fma(w, w, n2);
-    if (fabs(w) > mx) {
-      mx = fabs(w);
-      ix = i;
+  if (cached) {
+#pragma unroll
+    for (int c = 0; c < kAsmCache; ++c) {
+      const int i = t + c * kAsmThreads;
+      const double w = (i < nk) ? wcomp(i) : 0.0;
+      wc[c] = w;
+      n2 = fma(w, w, n2);
+      if (i < nk && fabs(w) > mx) {
+        mx = fabs(w);
+        ix = i;
+      }
+    }
+  } else {
+    for (int i = t; i < nk; i += kAsmThreads) {
+      const double w = wcomp(i);
+      n2 = fma(w, w, n2);
+      if (fabs(w) > mx) {
+        mx = fabs(w);
+        ix = i;
+      }
     }
   }
   s_n2[t] = n2;
@@ -1290,19 +1309,41 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
   const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
   if (W) {
     double* col = W + pos * n;
-    for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+    if (cached) {
+#pragma unroll
+      for (int c = 0; c < kAsmCache; ++c) {
+        const int i = t + c * kAsmThreads;
+        if (i < nk) col[sub.idx[i]] = wc[c] * scale;
+      }
+    } else {
+      for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
+    }
   } else {
     // Mixed mode: the column goes straight into its BF16 digit slices.
     const int f = tc_scale_exp(fabs(wmax * scale));
     if (t == 0) ws.fcol[pos] = f;
     __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
     const double s2 = ldexp(scale, -f);  // exact: scale * 2^-f
-    for (int i = t; i < nk; i += kAsmThreads) {
-      __nv_bfloat16 d[kTcSlices];
-      tc_split_scaled(wcomp(i), s2, d);
-      const int j = sub.idx[i];
+    if (cached) {
 #pragma unroll
-      for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
+      for (int c = 0; c < kAsmCache; ++c) {
+        const int i = t + c * kAsmThreads;
+        if (i < nk) {
+          __nv_bfloat16 d[kTcSlices];
+          tc_split_scaled(wc[c], s2, d);
+          const int j = sub.idx[i];
+#pragma unroll
+          for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
+        }
+      }
+    } else {
+      for (int i = t; i < nk; i += kAsmThreads) {
+        __nv_bfloat16 d[kTcSlices];
+        tc_split_scaled(wcomp(i), s2, d);
+        const int j = sub.idx[i];
+#pragma unroll
+        for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
+      }
     }
   }
 }
