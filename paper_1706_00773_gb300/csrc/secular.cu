@@ -70,7 +70,21 @@ __device__ __forceinline__ void group_sync(int g) {
   }
 }
 
-enum { ACC_M = 0, ACC_MN = 1, ACC_MG = 2 };
+// ACC_MN: M and N in FP64 (the zero finder, FP64 mode); ACC_MN32: M in FP64,
+// N (used only for Newton derivatives and first-order updates, which tolerate
+// FP32 relative error) in FP32 from the FP32 copy of U'; ACC_MG: M and the
+// terms on the point (the counts).  Only ACC_MG counts #{lam_i < x}: inside a
+// root's bracket that number is the pole index.
+enum { ACC_M = 0, ACC_MN = 1, ACC_MG = 2, ACC_MN32 = 3 };
+
+template <bool C, typename T, typename F>
+struct pick_type {
+  using type = T;
+};
+template <typename T, typename F>
+struct pick_type<false, T, F> {
+  using type = F;
+};
 
 // Sum over the kept terms of u_i u_i^T * r_i (r_i = 1/(x - lam_i)) into A and,
 // per MODE, of u_i u_i^T r_i^2 into B (ACC_MN) or, for terms sitting exactly on
@@ -82,20 +96,23 @@ template <int K, int E, int e, int MODE>
 __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
                                           const double* __restrict__ Us, int ld, int n,
                                           double lam_o, bool absolute, double tau, int skip_a,
-                                          int skip_b, double* sA, double* sB, int lane) {
+                                          int skip_b, double* sA, double* sB, int lane,
+                                          const float* __restrict__ Usf = nullptr) {
   constexpr int NS = nslots<K, E, e>();
   constexpr int KP = K + 1;
-  double A[NS], B[NS];
+  using BT = typename pick_type<MODE == ACC_MN32, float, double>::type;
+  double A[NS];
+  BT B[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     A[s] = 0.0;
-    B[s] = 0.0;
+    B[s] = (BT)0;
   }
   int below = 0;
   for (int i = lane; i < n; i += 32) {
     const double li = __ldg(lam + i);
     const double d = absolute ? (tau - li) : (tau - (li - lam_o));
-    below += (d > 0.0) ? 1 : 0;
+    if (MODE == ACC_MG) below += (d > 0.0) ? 1 : 0;
     double u[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) u[c] = __ldg(Us + (size_t)c * ld + i);
@@ -106,7 +123,7 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
         if (owner_of<K, E>(a) == e) {
 #pragma unroll
           for (int b = a; b < K; ++b) {
-            B[s] = fma(u[a], u[b], B[s]);
+            B[s] = (BT)fma(u[a], u[b], (double)B[s]);
             ++s;
           }
         }
@@ -119,6 +136,12 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
       double t[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) t[c] = u[c] * r;
+      float tf[K];
+      if (MODE == ACC_MN32) {
+        const float rf = (float)r;
+#pragma unroll
+        for (int c = 0; c < K; ++c) tf[c] = __ldg(Usf + (size_t)c * ld + i) * rf;
+      }
       int s = 0;
 #pragma unroll
       for (int a = 0; a < K; ++a) {
@@ -126,19 +149,21 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
 #pragma unroll
           for (int b = a; b < K; ++b) {
             A[s] = fma(t[a], u[b], A[s]);
-            if (MODE == ACC_MN) B[s] = fma(t[a], t[b], B[s]);
+            if (MODE == ACC_MN) B[s] = (BT)fma(t[a], t[b], (double)B[s]);
+            if (MODE == ACC_MN32) B[s] = (BT)fmaf(tf[a], tf[b], (float)B[s]);
             ++s;
           }
         }
       }
     }
   }
+  double B64[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     A[s] = warp_sum(A[s]);
-    if (MODE != ACC_M) B[s] = warp_sum(B[s]);
+    B64[s] = (MODE != ACC_M) ? warp_sum((double)B[s]) : 0.0;
   }
-  below = __reduce_add_sync(0xffffffffu, below);
+  if (MODE == ACC_MG) below = __reduce_add_sync(0xffffffffu, below);
   if (lane == 0) {
     int s = 0;
 #pragma unroll
@@ -149,8 +174,8 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
           sA[a * KP + b] = A[s];
           sA[b * KP + a] = A[s];
           if (MODE != ACC_M) {
-            sB[a * KP + b] = B[s];
-            sB[b * KP + a] = B[s];
+            sB[a * KP + b] = B64[s];
+            sB[b * KP + a] = B64[s];
           }
           ++s;
         }
@@ -165,19 +190,19 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
                                                 const double* __restrict__ Us, int ld, int n,
                                                 double lam_o, bool absolute, double tau,
                                                 int skip_a, int skip_b, double* sA, double* sB,
-                                                int lane) {
+                                                int lane, const float* __restrict__ Usf = nullptr) {
   // e is warp-uniform: each warp of a group runs the code for its own rows.
   if (E == 1 || e == 0)
     return accumulate<K, E, 0, MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a, skip_b, sA, sB,
-                                     lane);
+                                     lane, Usf);
   if (E > 1 && e == 1)
     return accumulate<K, E, (E > 1 ? 1 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
-                                                   skip_b, sA, sB, lane);
+                                                   skip_b, sA, sB, lane, Usf);
   if (E > 2 && e == 2)
     return accumulate<K, E, (E > 2 ? 2 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
-                                                   skip_b, sA, sB, lane);
+                                                   skip_b, sA, sB, lane, Usf);
   return accumulate<K, E, (E > 3 ? 3 : 0), MODE>(lam, Us, ld, n, lam_o, absolute, tau, skip_a,
-                                                 skip_b, sA, sB, lane);
+                                                 skip_b, sA, sB, lane, Usf);
 }
 
 // ----------------------------------------------------------------------------
@@ -730,9 +755,12 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const float ho = (float)lam_o, th32 = (float)tau_c;
       accumulate32_group<K, E, true>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
                                (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
+    } else if (sub.Usf) {
+      accumulate_group<K, E, ACC_MN32>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b, sMg, sNg,
+                                       lane, sub.Usf);
     } else {
-      below = accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b,
-                                             sMg, sNg, lane);
+      accumulate_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b, sMg, sNg,
+                                     lane);
     }
     group_sync<E>(g);
     if (e == 0) {
@@ -833,9 +861,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       g12 = warp_sum(g12);
       g22 = warp_sum(g22);
       const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
-      // Inside the bracket #{lam_i < x} is the pole index p (FP32 sums and
-      // first-order updates leave it out).
-      if (ph32 || tay) below = has_a ? p : 0;
+      // Inside the bracket #{lam_i < x} is the pole index p.
+      below = has_a ? p : 0;
       const int count = below + __popc(posmask) - posD - sub.kplus;
       // FP32 phase: the count is exact when no eigenvalue of Z can change sign
       // under the error of the FP32 sums, which only enters the K x K block:
