@@ -34,6 +34,7 @@ METRIC = "updated eigenpairs/s (n=8192,k=8) vs plain FP64 path; p50/p99 update l
 UNIT = "eigenpairs/s"
 N_DEFAULT, K_DEFAULT = 8192, 8
 FP64_PEAK_GFLOPS = 1250.0  # 152 SMs x 2 DFMA/clk x 2 flop x ~2.07 GHz (nominal FP64 rate)
+FP32_PEAK_GFLOPS = 80500.0  # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (CUDA-core FP32, no tensor cores)
 WORKLOAD = ("general rank-k update: n=8192, k=8, Q Haar FP64, lam = +-10^U[-3,3], "
             "K ~ N(0,1)/sqrt(n), sigma=+1 (seeded synthetic)")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "roofline_traffic.json")
@@ -144,10 +145,19 @@ def max_over_ranks(world, v: float) -> float:
 
 
 # ---------------------------------------------------------------------------
-def secular_flops(n_keep: int, k: int, evals: int) -> float:
-    """Algorithmic FP64 flops of the zero finder: every evaluation reduces n' terms
-    into M and N (k(k+1) each) plus the shift and reciprocal (2)."""
-    return float(evals) * n_keep * (2 * k * (k + 1) + 2)
+def secular_flops(n_keep: int, k: int, evals64: int, evals32: int, mixed: bool):
+    """Algorithmic flops of the zero finder per launch, by pipe.  An evaluation
+    reduces n' terms into M (k(k+1) flops: the upper triangle's FMAs) and N
+    (k(k+1)) plus the shift and reciprocal (2).  FP64 mode: all of it in FP64.
+    Mixed mode: FP64 evaluations take M, the shift and the reciprocal in FP64 and
+    N in FP32; coarse evaluations are FP32 throughout."""
+    per_m = k * (k + 1) + 2
+    per_n = k * (k + 1)
+    if not mixed:
+        return float(evals64) * n_keep * (per_m + per_n), 0.0
+    f64 = float(evals64) * n_keep * per_m
+    f32 = float(evals64) * n_keep * per_n + float(evals32) * n_keep * (per_m + per_n)
+    return f64, f32
 
 
 def load_traffic(kernel: str):
@@ -585,25 +595,38 @@ def main():
                                         "ms_slice", "ms_gemm")}
     n_keep = n - int(reps[-1]["n_deflated"])
     evals = statistics.fmean(r["iters_total"] for r in reps)
-    roots_flops = secular_flops(n_keep, k, evals)
-    roots_ach = roots_flops / (stage["ms_roots"] / 1000.0) / 1e9
-    roof_roots = {"kernel": "roots_kernel", "bound": "alu", "achieved": roots_ach, "peak": FP64_PEAK_GFLOPS,
-                  "unit": "GFLOP/s", "frac": roots_ach / FP64_PEAK_GFLOPS, "traffic": load_traffic("roots_kernel"),
+    evals32 = statistics.fmean(r["iters32_total"] for r in reps)
+    taylor = statistics.fmean(r["taylor_total"] for r in reps)
+    mixed = main_mode == eu.EIG_MIXED
+    f64, f32 = secular_flops(n_keep, k, evals, evals32, mixed)
+    roots_s = stage["ms_roots"] / 1000.0
+    roots_ach = f64 / roots_s / 1e9
+    roof_roots = {"kernel": "roots_grouped_kernel<8>", "bound": "alu", "achieved": roots_ach,
+                  "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": roots_ach / FP64_PEAK_GFLOPS,
+                  "traffic": load_traffic("roots_grouped_kernel"),
                   "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
-                  "work": "%.0f evaluations x n'(2k(k+1)+2) FP64 flops per launch" % evals}
+                  "work": ("%.0f FP64 evaluations x n'(k(k+1)+2) FP64 flops per launch (M, shift, reciprocal)"
+                           % evals) if mixed else ("%.0f evaluations x n'(2k(k+1)+2) FP64 flops per launch" % evals),
+                  "fp32": ({"achieved": f32 / roots_s / 1e9, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
+                            "frac": f32 / roots_s / 1e9 / FP32_PEAK_GFLOPS,
+                            "work": "%.0f FP32 evaluations x n'(2k(k+1)+2) + N of the FP64 ones, n' k(k+1)" % evals32}
+                           if mixed else None),
+                  "first_order_updates": taylor}
     if main_mode == eu.EIG_MIXED:
         gflops = 15 * 2.0 * n ** 3
         peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1000.0
         g_ach = gflops / (stage["ms_gemm"] / 1000.0) / 1e9
-        roof_gemm = {"kernel": "gemm_tc_kernel", "bound": "tensor", "achieved": g_ach / 1000.0, "peak": peak_t / 1000.0,
-                     "unit": "TFLOP/s", "frac": g_ach / peak_t, "traffic": load_traffic("gemm_tc_kernel"),
+        roof_gemm = {"kernel": "gemm_tc_grouped_kernel", "bound": "tensor", "achieved": g_ach / 1000.0,
+                     "peak": peak_t / 1000.0, "unit": "TFLOP/s", "frac": g_ach / peak_t,
+                     "traffic": load_traffic("gemm_tc_grouped_kernel"),
                      "peak_source": "bf16 dense, sustained, %s (MEASURED_PEAKS.json)" % psrc,
                      "work": "15 BF16 slice-pair products x 2 n^3 (useful FP64-equivalent 2 n^3 = %.3g)" % (2.0 * n ** 3)}
     else:
         gflops = 2.0 * n ** 3
         g_ach = gflops / (stage["ms_gemm"] / 1000.0) / 1e9
-        roof_gemm = {"kernel": "gemm_f64_kernel", "bound": "alu", "achieved": g_ach, "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": g_ach / FP64_PEAK_GFLOPS, "traffic": load_traffic("gemm_f64_kernel"),
+        roof_gemm = {"kernel": "gemm_f64_grouped_kernel", "bound": "alu", "achieved": g_ach, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": g_ach / FP64_PEAK_GFLOPS,
+                     "traffic": load_traffic("gemm_f64_grouped_kernel"),
                      "peak_source": "FP64 pipe (recipe nominal)", "work": "2 n^3 flops"}
     dominant = roof_roots if stage["ms_roots"] >= stage["ms_gemm"] else roof_gemm
     other = roof_gemm if dominant is roof_roots else roof_roots
@@ -617,6 +640,7 @@ def main():
             "fp64_path": fp64,
             "speedup_vs_fp64_path": (R["value"] / fp64["value"]) if fp64 else None,
             "stages_ms": stage, "evals_per_root": evals / max(1, n_keep),
+            "fp32_evals_per_root": evals32 / max(1, n_keep), "first_order_updates_per_root": taylor / max(1, n_keep),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
             "batched": batched,
