@@ -382,3 +382,61 @@ def test_residuals_at_rounding_level(eu, handle):
         assert rc == 0
         res = oracle.residuals(prob["Q"], prob["lam"], prob["K"], prob["sigma"], mu, X)
         assert np.max(res) <= 1e-13 * norm2_A(prob["lam"], prob["K"])
+
+
+# ---------------------------------------------------------------------------
+# Mixed mode: the zero finder's FP32 coarse phase and the FP32 pole counts
+# (certified, with FP64 fallbacks) against the oracle on hard spectra
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,sigma,k", [("clustered", "mixed", 3), ("clustered", "psd", 8), ("logspec", "nsd", 5),
+                                          ("logspec", "mixed", 12), ("uniform", "mixed", 16)])
+def test_mixed_coarse_phase_on_hard_spectra(eu, handle, handle_mixed, kind, sigma, k):
+    n = 700
+    P = workloads.general(n, k, seed=4100 + k, sigma=sigma, lam_kind=kind)
+    rc, rep, mum, Xm = _run_update(eu, handle_mixed, P)
+    assert rc == 0 and rep["n_notconv"] == 0
+    rc64, _, mu64, _ = _run_update(eu, handle, P, want=eu.EIG_VALUES | eu.EIG_VECTORS)
+    assert rc64 == 0
+    assert np.max(np.abs(mum - mu64)) <= 1e-12 * norm2_A(P["lam"], P["K"])
+    _check_full(P, mum, Xm)
+
+
+def test_mixed_repeated_poles_and_planted_deflation(eu, handle_mixed):
+    """Exactly repeated eigenvalues (FP32 differences of zero: the FP64 paths take
+    over) and rows of U that deflate."""
+    P = workloads.general(500, 4, seed=77, sigma="mixed", lam_kind="uniform")
+    lam = P["lam"].copy()
+    lam[100:104] = lam[100]          # a four-fold pole
+    lam[300] = lam[301] = lam[300]   # and a double one
+    P["lam"] = lam
+    Q = P["Q"]
+    P["K"] = P["K"] - Q[:, 200:210] @ (Q[:, 200:210].T @ P["K"])
+    rc, rep, mu, X = _run_update(eu, handle_mixed, P, want=eu.EIG_VALUES | eu.EIG_VECTORS | eu.EIG_REPORT)
+    assert rc == 0 and rep["n_notconv"] == 0
+    w = np.linalg.eigvalsh(oracle.updated_matrix(P["Q"], P["lam"], P["K"], P["sigma"]))
+    scale = norm2_A(P["lam"], P["K"])
+    assert np.max(np.abs(mu - w)) <= 1e-12 * scale
+    res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu, X)
+    assert np.max(res) <= 1e-9 * scale
+
+
+def test_mixed_indefinite_workload_matches_oracle(eu, handle_mixed):
+    """The one-row-one-column workload (1e-8 clusters, planted deflation) in
+    mixed mode, sampled against the oracle."""
+    import torch
+
+    W = workloads.indefinite_rank2(seed=1000, n=4096)
+    n = W["lam"].shape[0]
+    a = torch.from_numpy(W["a"].copy()).to("cuda:0")
+    K = torch.empty((2, n), dtype=torch.float64, device="cuda:0").t()
+    sig = eu.eig_make_rank2(n, W["j"], a, K)
+    P = dict(Q=W["Q"], lam=W["lam"], K=host(K), sigma=np.array(sig, dtype=np.int8))
+    rc, rep, mu, X = _run_update(eu, handle_mixed, P)
+    assert rc == 0 and rep["n_notconv"] == 0 and rep["iters32_total"] > 0
+    nk = n - int(rep["n_deflated"])  # roots of the sub-problem
+    sel = np.unique(np.concatenate([[0, nk // 2, nk - 1], np.random.default_rng(9).choice(nk, 40, replace=False)]))
+    ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], sel=sel)
+    scale = norm2_A(P["lam"], P["K"])
+    assert np.max(np.abs(mu[ref["pos"]] - ref["mu"])) <= MU_TOL * scale
+    res = oracle.residuals(P["Q"], P["lam"], P["K"], P["sigma"], mu[ref["pos"]], X[:, ref["pos"]])
+    assert np.max(res) <= RES_TOL * scale
