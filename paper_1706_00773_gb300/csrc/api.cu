@@ -946,20 +946,25 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   const int ld = (int)align_up((size_t)n, 32);
   const size_t cap = (size_t)(max_m < n ? max_m : n);
   // workspace: the secular carve (values only) + window ints + W_sel
+  const bool mixed = (h->mode == EIG_MIXED);
   const size_t base = align_up(plan(nullptr, n, k, false, false, false).bytes, 256);
-  const size_t need = base + 256 + (X ? sizeof(double) * (size_t)n * (cap > 0 ? cap : 1) : 0);
+  // FP32 copies for the mixed-mode zero finder, then W_sel
+  const size_t f32_bytes = mixed ? align_up(sizeof(float2) * ld, 256) + align_up(sizeof(float) * ld * Kp, 256) : 0;
+  const size_t need = base + 256 + f32_bytes + (X ? sizeof(double) * (size_t)n * (cap > 0 ? cap : 1) : 0);
   int rc = ensure_ws(h, need);
   if (rc) return rc;
   Carve c = plan(h->ws, n, k, false, false, false);
   int* win = reinterpret_cast<int*>(h->ws + base);               // 8 ints + 2 count slots
   double* pts = reinterpret_cast<double*>(h->ws + base + 128);    // vl, vu
-  double* Wsel = X ? reinterpret_cast<double*>(h->ws + base + 256) : nullptr;
+  float2* lamf = mixed ? reinterpret_cast<float2*>(h->ws + base + 256) : nullptr;
+  float* Usf = mixed ? reinterpret_cast<float*>(h->ws + base + 256 + align_up(sizeof(float2) * ld, 256)) : nullptr;
+  double* Wsel = X ? reinterpret_cast<double*>(h->ws + base + 256 + f32_bytes) : nullptr;
   const double xv[2] = {vl, vu};
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
   CK(launch_project_f64(n, k, Q, K, c.U, s));
   CK(launch_deflate(n, k, Kp, lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
-                    c.lam_defl, c.st, s));
+                    c.lam_defl, c.st, s, lamf, Usf));
   Sub sub;
   sub.n_dev = &c.st->n_keep;
   sub.ld = ld;
@@ -970,6 +975,8 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   sub.idx = c.idx_keep;
   sub.st = c.st;
   sub.negmask = negmask;
+  sub.lamf = lamf;
+  sub.Usf = Usf;
   CK(launch_counts(sub, pts, 2, win + 8, s));
   CK(launch_select_window(sub, c.st, c.lam_defl, vl, vu, win + 8, win, s));
   int hw[8];

@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
     int64_t n, int k, int K, const double* __restrict__ lam, const double* __restrict__ U,
     unsigned long long negmask, double* __restrict__ lam_keep, double* __restrict__ Us, int ld,
     int* __restrict__ idx_keep, int* __restrict__ idx_defl, double* __restrict__ lam_defl,
-    DevStatus* st) {
-  deflate_body(n, k, K, lam, U, negmask, lam_keep, Us, ld, idx_keep, idx_defl, lam_defl, st, nullptr);
+    DevStatus* st, float2* __restrict__ lamf, float* __restrict__ Usf) {
+  deflate_body(n, k, K, lam, U, negmask, lam_keep, Us, ld, idx_keep, idx_defl, lam_defl, st, nullptr, lamf,
+               Usf);
 }
 
 // One CTA per update of the table.
@@ -202,9 +203,9 @@ cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s)
 cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const double* U,
                            unsigned long long negmask, double* lam_keep, double* Us, int ld,
                            int* idx_keep, int* idx_defl, double* lam_defl, DevStatus* st,
-                           cudaStream_t s) {
+                           cudaStream_t s, float2* lamf, float* Usf) {
   deflate_kernel<<<1, kDeflThreads, 0, s>>>(n, k, K, lam, U, negmask, lam_keep, Us, ld, idx_keep,
-                                            idx_defl, lam_defl, st);
+                                            idx_defl, lam_defl, st, lamf, Usf);
   return cudaGetLastError();
 }
 

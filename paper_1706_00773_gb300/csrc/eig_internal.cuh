@@ -237,10 +237,11 @@ cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_
 cudaError_t launch_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items,
                                     int max_defl, bool vectors, bool mixed, cudaStream_t s);
 cudaError_t launch_make_rank2(int64_t n, int64_t j, const double* a, double* K, cudaStream_t s);
+// lamf / Usf (optional): FP32 copies of the kept lam' (hi, lo pairs) and U'.
 cudaError_t launch_deflate(int64_t n, int k, int K, const double* lam, const double* U,
                            unsigned long long negmask, double* lam_keep, double* Us, int ld,
                            int* idx_keep, int* idx_defl, double* lam_defl, DevStatus* st,
-                           cudaStream_t s);
+                           cudaStream_t s, float2* lamf = nullptr, float* Usf = nullptr);
 // Root counts #{mu < x}: at the poles [pt0, min(n', pt_end)) of the sub-problem
 // (x == nullptr; counts[q] for pole q) or at npts absolute points x.
 cudaError_t launch_counts(const Sub& sub, const double* x, int npts, int* counts, cudaStream_t s,

@@ -121,3 +121,27 @@ def test_select_full_size_sampled(eu, handle):
     assert np.max(np.abs(mu - ref["mu"])) <= 1e-13 * scale
     cos = np.abs(np.sum(X * ref["X"], axis=0))
     assert np.min(cos) >= 1 - 1e-9
+
+
+def test_select_mixed_mode_equals_the_full_mixed_update(eu):
+    """Mixed mode: the interval's zero finder runs the FP32 coarse phase and the
+    certified FP32 pole counts exactly like the full update, so the selected
+    eigenvalues are the full update's, bit for bit; X_sel comes from the FP64
+    GEMM, X from the split-BF16 one (agreement within the latter's error)."""
+    import torch
+
+    h = eu.eig_update_init(0, eu.EIG_MIXED)
+    try:
+        for n, k, sigma, kind in [(900, 8, "psd", "logspec"), (1300, 5, "mixed", "clustered")]:
+            P = workloads.general(n, k, seed=1600 + n, sigma=sigma, lam_kind=kind)
+            mu_all, X_all = _full(eu, h, P)
+            mid = lambda i: 0.5 * (mu_all[i - 1] + mu_all[i])  # noqa: E731
+            for vl, vu in [(mid(n // 4), mid(n // 4 + 60)), (-np.inf, mid(40))]:
+                rc, m, mu, X = _select(eu, h, P, vl, vu)
+                assert rc == 0
+                sel = np.nonzero((mu_all >= vl) & (mu_all < vu))[0]
+                assert m == len(sel)
+                assert np.array_equal(mu, mu_all[sel])
+                assert np.max(np.abs(X - X_all[:, sel])) <= 1e-10
+    finally:
+        eu.eig_update_destroy(h)
