@@ -395,6 +395,35 @@ def run_serving(eu, dev, mode, residents=12, nmin=1024, nmax=4096, chain=6, load
                             residents, nmin, nmax, chain, load)}
 
 
+def pin_to_gpu_numa(local: int) -> str:
+    """Run the host side on the CPUs of the GPU's NUMA node (pinned buffers are
+    then allocated there).  Returns a note for the JSON line; leaves the affinity
+    alone when the topology cannot be read."""
+    import torch
+
+    try:
+        pr = torch.cuda.get_device_properties(local)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/numa_node" % bus) as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return " (GPU NUMA node unknown)"
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if not part:
+                continue
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if not cpus:
+            return " (GPU NUMA node %d has no CPUs)" % node
+        os.sched_setaffinity(0, cpus)
+        return " on the GPU's NUMA node %d (CPUs %s)" % (node, spec)
+    except Exception as exc:  # topology not readable: keep the default placement
+        return " (NUMA placement not set: %s)" % type(exc).__name__
+
+
 def _time_ms(fn, reps):
     import torch
 
@@ -525,47 +554,101 @@ def main():
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e_value = None
+    e2e_note = None
+    e2e_serial_ms = None
     h2d = (n * n + n * k + n) * 8
     d2h = (n * n + n) * 8
     stream = torch.cuda.current_stream()
     if not args.no_e2e:
         # Host buffers hold the transposes row-major, i.e. the matrices column-major,
-        # so every copy is one contiguous transfer.
+        # so every copy is one contiguous transfer.  Two device buffer sets and two
+        # copy streams pipeline the steps: step i+1's inputs go up and step i's
+        # results come down while step i computes.  Every step's copies are inside
+        # the timed region (the first upload and the last download are not hidden).
+        numa = pin_to_gpu_numa(local)
         Qh = torch.from_numpy(np.ascontiguousarray(P["Q"].T)).pin_memory()
         Kh = torch.from_numpy(np.ascontiguousarray(P["K"].T)).pin_memory()
         lamh = torch.from_numpy(P["lam"].copy()).pin_memory()
-        Xh = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        lamo = torch.empty(n, dtype=torch.float64).pin_memory()
-        Qd_rm = torch.empty((n, n), dtype=torch.float64, device=dev)
-        Kd_rm = torch.empty((k, n), dtype=torch.float64, device=dev)
-        Xd_rm = torch.empty((n, n), dtype=torch.float64, device=dev)
-        lamd = torch.empty(n, dtype=torch.float64, device=dev)
-        want = eu.EIG_VALUES | eu.EIG_VECTORS
+        Xh = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+        lamo = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
+        Qd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
+        Kd = [torch.empty((k, n), dtype=torch.float64, device=dev) for _ in range(2)]
+        lamd = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+        Xd = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(2)]
+        up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        comp = stream
+        want = eu.EIG_VALUES | eu.EIG_VECTORS | eu.EIG_ASYNC
+        ev_in = [torch.cuda.Event() for _ in range(2)]     # inputs of a set are on the device
+        ev_done = [torch.cuda.Event() for _ in range(2)]   # the update that used a set finished
+        ev_out = [torch.cuda.Event() for _ in range(2)]    # results of a set are on the host
 
-        def e2e_step():
-            Qd_rm.copy_(Qh, non_blocking=True)
-            Kd_rm.copy_(Kh, non_blocking=True)
-            lamd.copy_(lamh, non_blocking=True)
-            rc, _ = eu.eig_update_rank_k(h, Qd_rm.t(), lamd, Kd_rm.t(), P["sigma"], want, Q_out=Xd_rm.t(),
-                                         stream=stream)
-            assert rc == 0
-            Xh.copy_(Xd_rm, non_blocking=True)
-            lamo.copy_(lamd, non_blocking=True)
+        def upload(b, after=None):
+            with torch.cuda.stream(up):
+                if after is not None:
+                    up.wait_event(after)
+                Qd[b].copy_(Qh, non_blocking=True)
+                Kd[b].copy_(Kh, non_blocking=True)
+                lamd[b].copy_(lamh, non_blocking=True)
+                ev_in[b].record(up)
 
-        e2e_steps = max(1, min(args.steps, 3))
-        e2e_step()
+        def run_steps(count):
+            upload(0)
+            for i in range(count):
+                b = i % 2
+                comp.wait_event(ev_in[b])
+                if i >= 2:
+                    comp.wait_event(ev_out[b])  # X[b] / lam[b] downloaded before reuse
+                if i + 1 < count:
+                    # the set's last results (lambda is in/out) must be downloaded first
+                    upload(1 - b, after=ev_out[1 - b] if i >= 1 else None)
+                rc, _ = eu.eig_update_rank_k(h, Qd[b].t(), lamd[b], Kd[b].t(), P["sigma"], want,
+                                             Q_out=Xd[b].t(), stream=comp)
+                assert rc == 0
+                ev_done[b].record(comp)
+                with torch.cuda.stream(down):
+                    down.wait_event(ev_done[b])
+                    Xh[b].copy_(Xd[b], non_blocking=True)
+                    lamo[b].copy_(lamd[b], non_blocking=True)
+                    ev_out[b].record(down)
+            comp.wait_stream(up)
+            comp.wait_stream(down)
+
+        e2e_steps = max(2, min(args.steps, 5))
+        run_steps(2)
         torch.cuda.synchronize()
+        assert eu.eig_update_query(h, eu.EIG_Q_LAST_STATUS) == 0
         barrier(world)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        f1.record(stream)
+        f0.record(comp)
+        up.wait_stream(comp)
+        down.wait_stream(comp)
+        run_steps(e2e_steps)
+        f1.record(comp)
         torch.cuda.synchronize()
+        assert eu.eig_update_query(h, eu.EIG_Q_LAST_STATUS) == 0
+        assert np.all(np.diff(lamo[(e2e_steps - 1) % 2].numpy()) >= 0)
         e2e_ms = max_over_ranks(world, f0.elapsed_time(f1))
         e2e_value = world * n * e2e_steps / (e2e_ms / 1000.0)
-        del Qd_rm, Kd_rm, Xd_rm
+        # Latency of one update with its copies, nothing overlapped (context for the
+        # pipelined rate): upload, update, download back to back on one stream.
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(comp)
+        Qd[0].copy_(Qh, non_blocking=True)
+        Kd[0].copy_(Kh, non_blocking=True)
+        lamd[0].copy_(lamh, non_blocking=True)
+        rc, _ = eu.eig_update_rank_k(h, Qd[0].t(), lamd[0], Kd[0].t(), P["sigma"], eu.EIG_VALUES | eu.EIG_VECTORS,
+                                     Q_out=Xd[0].t(), stream=comp)
+        assert rc == 0
+        Xh[0].copy_(Xd[0], non_blocking=True)
+        lamo[0].copy_(lamd[0], non_blocking=True)
+        g1.record(comp)
+        torch.cuda.synchronize()
+        e2e_serial_ms = g0.elapsed_time(g1)
+        e2e_note = ("pipelined over %d steps: step i+1's upload and step i's download overlap step i's "
+                    "update on separate streams; host buffers pinned%s" % (e2e_steps, numa))
+        del Qd, Kd, Xd
     eu.eig_update_destroy(h)
 
     # ---- the plain FP64 path on the same inputs (the comparison the metric names)
@@ -641,7 +724,8 @@ def main():
             "speedup_vs_fp64_path": (R["value"] / fp64["value"]) if fp64 else None,
             "stages_ms": stage, "evals_per_root": evals / max(1, n_keep),
             "fp32_evals_per_root": evals32 / max(1, n_keep), "first_order_updates_per_root": taylor / max(1, n_keep),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "how": e2e_note, "serial_update_with_copies_ms": e2e_serial_ms},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
             "batched": batched,
             "serving": serving,
