@@ -134,14 +134,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, v: float) -> float:
+    """The slowest rank's time (NCCL on the GPUs; any other backend on the host)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world: int, units_per_rank: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1000.0)
 
 
 # ---------------------------------------------------------------------------
@@ -283,7 +290,7 @@ def run_mode(eu, h, P, dev, steps, warmup, world):
     ms = max_over_ranks(world, e0.elapsed_time(e1))
     lat = sorted(r["ms_total"] for r in reps)
     del Q, K, X
-    return {"ms": ms, "value": world * n * steps / (ms / 1000.0), "reps": reps,
+    return {"ms": ms, "value": aggregate_rate(world, n, steps, ms), "reps": reps,
             "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
 
 
@@ -629,7 +636,7 @@ def main():
         assert eu.eig_update_query(h, eu.EIG_Q_LAST_STATUS) == 0
         assert np.all(np.diff(lamo[(e2e_steps - 1) % 2].numpy()) >= 0)
         e2e_ms = max_over_ranks(world, f0.elapsed_time(f1))
-        e2e_value = world * n * e2e_steps / (e2e_ms / 1000.0)
+        e2e_value = aggregate_rate(world, n, e2e_steps, e2e_ms)
         # Latency of one update with its copies, nothing overlapped (context for the
         # pipelined rate): upload, update, download back to back on one stream.
         g0 = torch.cuda.Event(enable_timing=True)
