@@ -297,10 +297,12 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
       T.class_items[c] += (int)items[i].P->n;
     }
   }
-  for (auto& cd : T.classes) {
+  for (size_t ci = 0; ci < T.classes.size(); ++ci) {
+    ClassDesc& cd = T.classes[ci];
+    cd.perm = reinterpret_cast<int*>(b.take(sizeof(int) * (size_t)T.class_items[ci]));
     cd.pk = reinterpret_cast<int*>(b.take(sizeof(int) * (cd.count + 1)));
     cd.pd = reinterpret_cast<int*>(b.take(sizeof(int) * (cd.count + 1)));
-    cd.counter = reinterpret_cast<int*>(b.take(sizeof(int)));
+    cd.counter = reinterpret_cast<int*>(b.take(sizeof(int) * 3));
   }
   // --- shared contiguous regions ---
   T.d_st = reinterpret_cast<DevStatus*>(b.take(sizeof(DevStatus) * count));
@@ -454,8 +456,9 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   }
   MARK(3);
   for (size_t c = 0; c < T.classes.size(); ++c) {
+    CK(launch_order_roots_grouped(T.d_desc, T.classes[c], T.class_items[c], s));
     CK(launch_roots_grouped(T.d_desc, T.classes[c], T.class_items[c], h->max_iter, h->num_sms, s));
-    ++nl;
+    nl += 2;
   }
   MARK(4);
   if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));

@@ -216,7 +216,8 @@ struct ClassDesc {
   const int* ids;
   int* pk;
   int* pd;
-  int* counter;
+  int* counter;   // 3 ints: the zero finder's work counter, then two partition counters
+  int* perm;      // class items in the order the zero finder takes them (null: natural order)
 };
 
 // ---- launch wrappers (defined in the .cu files) ----------------------------
@@ -234,6 +235,9 @@ cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStrea
 cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s);
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
                                  int num_sms, cudaStream_t s);
+// Order the zero finder's work: roots in pole intervals that hold several roots
+// (the ones that need the most evaluations) first, so they do not finish last.
+cudaError_t launch_order_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s);
 cudaError_t launch_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items,
                                     int max_defl, bool vectors, bool mixed, cudaStream_t s);
 cudaError_t launch_make_rank2(int64_t n, int64_t j, const double* a, double* K, cudaStream_t s);

@@ -1189,7 +1189,10 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
   const int g = warp / E, e = warp - (warp / E) * E;
   const int total = c.pk[c.count];
   for (;;) {
-    if (e == 0 && lane == 0) s_m[g] = atomicAdd(c.counter, 1);
+    if (e == 0 && lane == 0) {
+      const int slot = atomicAdd(c.counter, 1);
+      s_m[g] = (slot < total && c.perm) ? c.perm[slot] : slot;
+    }
     group_sync<E>(g);
     const int item = s_m[g];
     if (item >= total) break;
@@ -1471,7 +1474,34 @@ __global__ void class_prefix_kernel(const ProbDesc* __restrict__ P, ClassDesc c)
     c.pk[i + 1] = sk;
     c.pd[i + 1] = sd;
   }
-  *c.counter = 0;
+  c.counter[0] = 0;
+  c.counter[1] = 0;
+  c.counter[2] = 0;
+}
+
+// Items of roots in pole intervals with several roots go to the front of perm,
+// the rest to the back (the order inside each part does not matter: every root
+// is solved independently).
+__global__ void order_roots_grouped_kernel(const ProbDesc* __restrict__ P, ClassDesc c) {
+  const int total = c.pk[c.count];
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+    const int q = find_owner(c.pk, c.count, item);
+    const ProbDesc& d = P[c.ids[q]];
+    bool hard = false;
+    if (!input_invalid(d.st)) {
+      const int n = d.st->n_keep, m = item - c.pk[q];
+      int lo = 0, hi = n;  // p = #{poles with count <= m}
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (d.pole_cnt[mid] <= m) lo = mid + 1; else hi = mid;
+      }
+      const int c_lo = lo > 0 ? d.pole_cnt[lo - 1] : 0;
+      const int c_hi = lo < n ? d.pole_cnt[lo] : n;
+      hard = (c_hi - c_lo) > 1;
+    }
+    if (hard) c.perm[atomicAdd(&c.counter[1], 1)] = item;
+    else c.perm[total - 1 - atomicAdd(&c.counter[2], 1)] = item;
+  }
 }
 
 // ---- eigenpairs in a value interval [vl, vu) ------------------------------------
@@ -1729,6 +1759,14 @@ cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max
 #undef C_
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_order_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s) {
+  if (!c.perm || max_items <= 0) return cudaSuccess;
+  int blocks = (max_items + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  order_roots_grouped_kernel<<<blocks, 256, 0, s>>>(P, c);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
