@@ -99,9 +99,11 @@ __device__ __forceinline__ int tc_scale_exp(double mx) {
 // shifted up), so that y = 2^-8 sum_p m_p 2^(-8p) up to 2^-41.  Slice p holds
 // m_p 2^(-8p) (exact in BF16).  tc_split_scaled takes x and the exact power-of-
 // two factor s with y = x * s, so the product is rounded only once.
-__device__ __forceinline__ void tc_split_scaled(double x, double s, __nv_bfloat16 (&out)[kTcSlices]) {
+// s40 = s * 2^40 (exact): callers that split many entries with one scale pass
+// it precomputed, leaving one FMA per entry on the FP64 pipe.
+__device__ __forceinline__ void tc_split_prescaled(double x, double s40, __nv_bfloat16 (&out)[kTcSlices]) {
   const double magic = 6755399441055744.0;  // 1.5 * 2^52
-  long long R = __double_as_longlong(fma(x, s * 1099511627776.0, magic)) - __double_as_longlong(magic);
+  long long R = __double_as_longlong(fma(x, s40, magic)) - __double_as_longlong(magic);
   int m[kTcSlices];
 #pragma unroll
   for (int p = kTcSlices - 1; p > 0; --p) {
@@ -113,6 +115,10 @@ __device__ __forceinline__ void tc_split_scaled(double x, double s, __nv_bfloat1
   m[0] = (int)R;
 #pragma unroll
   for (int p = 0; p < kTcSlices; ++p) out[p] = __float2bfloat16_rn(ldexpf((float)m[p], -8 * p));
+}
+
+__device__ __forceinline__ void tc_split_scaled(double x, double s, __nv_bfloat16 (&out)[kTcSlices]) {
+  tc_split_prescaled(x, s * 1099511627776.0, out);
 }
 
 __device__ __forceinline__ void tc_split(double r, __nv_bfloat16 (&out)[kTcSlices]) {

@@ -499,13 +499,20 @@ __global__ void slice_q_grouped_kernel(const ProbDesc* __restrict__ P, int count
   const int lds = (n + 63) / 64 * 64;
   const size_t plane = (size_t)lds * (size_t)n;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  // The thread's row is fixed: its scale is formed once (one FMA per entry left).
+  const int irow = i0 + tx;
+  int erow_i = 0;
+  double s40 = 0.0;
+  if (irow < n) {
+    erow_i = tc_scale_exp(__longlong_as_double((long long)d.rmax[irow]));
+    s40 = ldexp(1.0, 40 - erow_i);
+  }
   for (int jj = ty; jj < 32; jj += 8) {
-    const int i = i0 + tx, j = j0 + jj;
+    const int i = irow, j = j0 + jj;
     __nv_bfloat16 dd[kSlices];
     if (i < n && j < n) {
-      const int e = tc_scale_exp(__longlong_as_double((long long)d.rmax[i]));
-      tc_split_scaled(d.Q[(size_t)j * n + i], ldexp(1.0, -e), dd);
-      if (j == 0) d.erow[i] = e;
+      tc_split_prescaled(d.Q[(size_t)j * n + i], s40, dd);
+      if (j == 0) d.erow[i] = erow_i;
     } else {
 #pragma unroll
       for (int q = 0; q < kSlices; ++q) dd[q] = __double2bfloat16(0.0);

@@ -1353,14 +1353,14 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
     const int f = tc_scale_exp(fabs(wmax * scale));
     if (t == 0) ws.fcol[pos] = f;
     __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
-    const double s2 = ldexp(scale, -f);  // exact: scale * 2^-f
+    const double s2 = ldexp(scale, 40 - f);  // exact: scale * 2^(40-f), the split's prescale
     if (cached) {
 #pragma unroll
       for (int c = 0; c < kAsmCache; ++c) {
         const int i = t + c * kAsmThreads;
         if (i < nk) {
           __nv_bfloat16 d[kTcSlices];
-          tc_split_scaled(wc[c], s2, d);
+          tc_split_prescaled(wc[c], s2, d);
           const int j = sub.idx[i];
 #pragma unroll
           for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
@@ -1369,7 +1369,7 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
     } else {
       for (int i = t; i < nk; i += kAsmThreads) {
         __nv_bfloat16 d[kTcSlices];
-        tc_split_scaled(wcomp(i), s2, d);
+        tc_split_prescaled(wcomp(i), s2, d);
         const int j = sub.idx[i];
 #pragma unroll
         for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
