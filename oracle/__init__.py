@@ -153,6 +153,47 @@ def rank2_perturbation(n: int, j: int, a):
     return K, np.array([1, -1], dtype=np.int8)
 
 
+def repeated_runs(lam):
+    """Maximal runs [g0, g0 + m) of exactly equal lam with m >= 2 (lam ascending)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    runs = []
+    i, n = 0, lam.shape[0]
+    while i < n:
+        j = i + 1
+        while j < n and lam[j] == lam[i]:
+            j += 1
+        if j - i > 1:
+            runs.append((i, j - i))
+        i = j
+    return runs
+
+
+def group_rotate(Q, lam, U):
+    """Exactly repeated eigenvalues (the paper assumes distinct lam, Sec. 2.1).
+
+    On a run G of m >= 2 equal lam, A = Q diag(lam) Q^T does not change when
+    Q_G is replaced by Q_G H for any orthogonal m x m H, and U_G = Q_G^T K then
+    becomes H^T U_G.  With the complete QR U_G = H R (numpy, a library step) the
+    run's rows of U become R: rows past min(m, k) are zero and rows past
+    rank(U_G) are at rounding level, so the row deflation removes them and the
+    secular problem keeps the pole lam at most min(m, k) times.  The removed
+    pairs are (lam, Q_G H e_j): an orthonormal basis of the part of the
+    eigenspace that K does not touch.  Returns (Q~, U~); the inputs when lam
+    has no repeats."""
+    runs = repeated_runs(lam)
+    if not runs:
+        return Q, U
+    Qt = np.array(Q, dtype=np.float64, copy=True)
+    Ut = np.array(U, dtype=np.float64, copy=True)
+    k = Ut.shape[1]
+    for g0, m in runs:
+        H, R = np.linalg.qr(Ut[g0:g0 + m], mode="complete")
+        R[min(m, k):] = 0.0
+        Ut[g0:g0 + m] = R
+        Qt[:, g0:g0 + m] = Qt[:, g0:g0 + m] @ H
+    return Qt, Ut
+
+
 def deflation_mask(lam, U):
     """Rows u_i small enough to drop (the paper assumes all u_i != 0 and
     distinct lam, Sec. 2.1; it is silent on what to do otherwise).
@@ -263,7 +304,8 @@ def vectors(lam, U, sigma, origin, tau, rank=None):
 
 
 def update(Q, lam, K, sigma=None, want_vectors: bool = True, sel=None, nthreads: int | None = None):
-    """The whole update A' = Q diag(lam) Q^T + K Sigma K^T, by the paper's method.
+    """The whole update A' = Q diag(lam) Q^T + K Sigma K^T, by the paper's method
+    (with exactly repeated eigenvalues first rotated by ``group_rotate``).
 
     sel (optional) lists root indices m of the non-deflated sub-problem to solve
     (sampling for large n); then only those roots and vectors are returned.
@@ -276,11 +318,12 @@ def update(Q, lam, K, sigma=None, want_vectors: bool = True, sel=None, nthreads:
     k = K.shape[1]
     s = _sig(sigma, k)
     U = project(Q, K)
+    Q, U = group_rotate(Q, lam, U)  # no-op unless lam has exact repeats
     defl = deflation_mask(lam, U)
     keep = np.nonzero(~defl)[0]
     lam_p = lam[keep]
     U_p = U[keep]
-    out = dict(U=U, deflated=defl, keep=keep)
+    out = dict(U=U, deflated=defl, keep=keep, Q=Q)
     if sel is not None:
         r = roots(lam_p, U_p, s, sel=sel, nthreads=nthreads)
         mu = r["mu"]

@@ -168,6 +168,13 @@ def general(n: int, k: int, seed: int, sigma="psd", lam_kind: str = "uniform",
         lam = np.sort(np.concatenate([base, base[rng.choice(n - npairs, npairs, replace=False)] + 1e-8]))
     elif lam_kind == "constant":
         lam = np.full(n, 0.375)
+    elif lam_kind == "repeated":
+        # runs of exactly equal values: singles, pairs, and runs longer than k
+        sizes = []
+        while sum(sizes) < n:
+            sizes.append(int(rng.choice([1, 1, 1, 2, 3, k + 1, 2 * k + 3])))
+        sizes[-1] -= sum(sizes) - n
+        lam = np.repeat(_sorted_distinct_uniform(len(sizes), -1.0, 1.0, rng), sizes)
     else:
         raise ValueError(lam_kind)
     Q = haar(n, rng)
