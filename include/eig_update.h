@@ -114,7 +114,9 @@ typedef struct {
   double ms_slice;      /* EIG_MIXED: BF16 digit slices of Q (0 in EIG_FP64) */
   double ms_gemm;       /* X = Q W */
   int32_t launches;     /* kernels this update launched */
-  int32_t pad_;
+  int32_t n_runs;       /* runs of exactly equal old eigenvalues, each rotated
+                           inside its eigenspace before deflation so that at
+                           most k of its rows stay in the secular problem */
   int64_t iters32_total; /* EIG_MIXED: coarse FP32 evaluations of the zero finder
                             (iters_total counts the FP64 ones) */
   int64_t redo32_total;  /* EIG_MIXED: FP32 evaluations whose root count the
@@ -212,7 +214,7 @@ int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda,
  * memory up front) and latency-critical loops that cannot absorb a
  * cudaMalloc/cudaFree (cudaFree synchronises the device).  It computes what
  * eig_secular_values computes, for n <= EIG_STATIC_MAX_N and k <= EIG_MAX_K,
- * with every temporary in one fixed 3 MiB device array that the library
+ * with every temporary in one fixed 6 MiB device array that the library
  * defines at file scope; the caller passes inputs and outputs only, and no
  * handle is needed.  Larger problems return EIG_ETOOBIG.
  *   - Every GPU that loads the library holds that array until the process exits.

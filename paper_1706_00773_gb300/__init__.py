@@ -71,7 +71,7 @@ class eig_report(ctypes.Structure):
                 ("ms_project", ctypes.c_double), ("ms_deflate", ctypes.c_double),
                 ("ms_counts", ctypes.c_double), ("ms_roots", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_slice", ctypes.c_double), ("ms_gemm", ctypes.c_double),
-                ("launches", ctypes.c_int32), ("pad_", ctypes.c_int32), ("iters32_total", ctypes.c_int64),
+                ("launches", ctypes.c_int32), ("n_runs", ctypes.c_int32), ("iters32_total", ctypes.c_int64),
                 ("redo32_total", ctypes.c_int64), ("taylor_total", ctypes.c_int64)]
 
     def as_dict(self) -> dict:

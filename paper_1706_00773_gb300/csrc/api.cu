@@ -64,6 +64,9 @@ struct Carve {
   double* chk_out = nullptr;
   int* chk_cols = nullptr;
   DevStatus* st = nullptr;
+  double* Vr = nullptr;  // runs of equal lam: reflectors, scalars, (g0, m) list
+  double* taur = nullptr;
+  int* runs = nullptr;
   size_t bytes = 0;
 };
 
@@ -95,6 +98,9 @@ Carve plan(char* base, int64_t n, int k, bool vectors, bool xbuf, bool report, b
   c.sidx = reinterpret_cast<int*>(take(sizeof(int) * ld * 2));
   c.mu_sec = reinterpret_cast<double*>(take(sizeof(double) * ld));
   c.lam_old = reinterpret_cast<double*>(take(sizeof(double) * ld));
+  c.Vr = reinterpret_cast<double*>(take(sizeof(double) * (size_t)n * k));
+  c.taur = reinterpret_cast<double*>(take(sizeof(double) * ld));
+  c.runs = reinterpret_cast<int*>(take(sizeof(int) * ld));
   if (report) {
     c.chk_tmp = reinterpret_cast<double*>(take(sizeof(double) * 3 * (size_t)n * kCheckCols));
     c.chk_out = reinterpret_cast<double*>(take(sizeof(double) * (kCheckCols + kCheckCols * kCheckCols)));
@@ -248,6 +254,7 @@ struct Table {
   std::vector<ClassDesc> classes;
   std::vector<int> class_items;  // sum of n per class (grid bound)
   long long total_cols = 0, total_copy = 0;
+  int64_t max_n = 0;
   int total_rb = 0, total_sl = 0, total_gt = 0;
   // report (single update only)
   double* chk_tmp = nullptr;
@@ -362,6 +369,10 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     d.sidx = reinterpret_cast<int*>(b.take(sizeof(int) * ld * 2));
     d.mu_sec = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
     d.lam_old = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.Vr = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * k));
+    d.taur = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
+    d.runs = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    if (n > T.max_n) T.max_n = n;
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
       d.lamf = reinterpret_cast<float2*>(b.take(sizeof(float2) * ld));
       d.Usf = reinterpret_cast<float*>(b.take(sizeof(float) * ld * K));
@@ -444,7 +455,8 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   CK(cudaMemcpyAsync(T.d_desc, img.data(), img.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(T.d_st, 0, sizeof(DevStatus) * count, s));
   CK(launch_project_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
-  ++nl;
+  CK(launch_runs_qr_grouped(T.d_desc, count, T.max_n, s));
+  nl += 2;
   MARK(1);
   CK(launch_deflate_grouped(T.d_desc, count, s));
   ++nl;
@@ -470,13 +482,16 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   MARK(5);
   if (vectors) {
     if (mixed) {
+      CK(launch_runs_rotate_q_grouped(T.d_desc, count, h->num_sms, s));
       CK(cudaMemsetAsync(T.d_rmax, 0, T.rmax_bytes, s));
       CK(launch_slice_q_grouped(T.d_desc, count, T.d_rbpre, T.total_rb, T.d_slpre, T.total_sl, s));
-      nl += 2;
+      nl += 4;
       MARK(6);
       CK(launch_gemm_tc_grouped(T.d_desc, count, T.d_maps, T.d_gtpre, T.total_gt, s));
       ++nl;
     } else {
+      CK(launch_runs_apply_w_grouped(T.d_desc, count, h->num_sms, s));
+      ++nl;
       MARK(6);
       CK(launch_gemm_f64_grouped(T.d_desc, count, T.d_gtpre, T.total_gt, s));
       ++nl;
@@ -520,6 +535,7 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->iters32_total = st.iters32_total;
   rep->redo32_total = st.redo32_total;
   rep->taylor_total = st.taylor_total;
+  rep->n_runs = st.n_runs;
   rep->iters_max = st.iters_max;
   rep->n_notconv = st.n_notconv;
   rep->norm_A = st.lam_absmax + st.fro2;
@@ -856,7 +872,10 @@ int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda,
   if (rc) return rc;
   Carve c = plan(h->ws, n, k, false, false, false);
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
-  CK(launch_deflate(n, k, K, lambda, U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
+  // runs of equal lambda are rotated in a copy of U (the caller's U is input only)
+  CK(cudaMemcpyAsync(c.U, U, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+  CK(launch_runs_qr(n, k, lambda, c.U, c.Vr, c.taur, c.runs, c.st, s));
+  CK(launch_deflate(n, k, K, lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
                     c.lam_defl, c.st, s));
   Sub sub;
   sub.n_dev = &c.st->n_keep;
@@ -966,6 +985,7 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
   CK(launch_project_f64(n, k, Q, K, c.U, s));
+  CK(launch_runs_qr(n, k, lambda, c.U, c.Vr, c.taur, c.runs, c.st, s));
   CK(launch_deflate(n, k, Kp, lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
                     c.lam_defl, c.st, s, lamf, Usf));
   Sub sub;
@@ -1009,7 +1029,10 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   if (Wsel) CK(cudaMemsetAsync(Wsel, 0, sizeof(double) * (size_t)n * (size_t)m, s));
   RootOut ro{c.origin, c.tau, c.iters, c.rflags, c.alpha, c.beta, c.sidx};
   CK(launch_assemble_select(sub, ro, n, c.idx_defl, c.lam_defl, dlo, dsel, r0, r1, c.mu_sec, mu, Wsel, s));
-  if (X) CK(launch_gemm_f64(n, m, n, Q, n, Wsel, n, X, n, s));
+  if (X) {
+    CK(launch_runs_apply_w(n, k, c.Vr, c.taur, c.runs, c.st, Wsel, n, m, h->num_sms, s));  // W_sel <- B W_sel
+    CK(launch_gemm_f64(n, m, n, Q, n, Wsel, n, X, n, s));
+  }
   CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return status_of(*h->st_host);

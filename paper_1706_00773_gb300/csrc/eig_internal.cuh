@@ -48,7 +48,8 @@ struct DevStatus {
   long long iters32_total; // FP32 (coarse-phase) evaluations
   long long redo32_total;  // FP32 evaluations whose count was not certified
   long long taylor_total;  // evaluations by a first-order update of the K x K sums
-  long long pad_;
+  int n_runs;              // runs of exactly repeated lam rotated before deflation
+  int run_rows;            // rows in those runs
 };
 
 // The non-deflated sub-problem in the layout the secular kernels read.  Its
@@ -171,6 +172,9 @@ struct ProbDesc {
   DevStatus* st;
   float2* lamf;            // mixed mode: FP32 copies for the coarse zero-finder phase
   float* Usf;
+  double* Vr;              // reflectors of the runs of equal lam (n x k), see runs.cu
+  double* taur;            // their scalars (n)
+  int* runs;               // (g0, m) pairs (n ints)
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
@@ -235,6 +239,17 @@ cudaError_t launch_project_grouped(const ProbDesc* P, int count, const long long
                                    long long total_cols, cudaStream_t s);
 // Deflation + compaction for every update (one CTA each); also keeps lam_old.
 cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s);
+// Runs of exactly repeated lam (runs.cu): QR of each run's rows of U before
+// deflation, then B applied to W's rows (FP64 GEMM paths) or Q~ = Q B written
+// to Xout (split-BF16 path).
+cudaError_t launch_runs_qr(int64_t n, int k, const double* lam, double* U, double* V, double* tau, int* runs,
+                           DevStatus* st, cudaStream_t s);
+cudaError_t launch_runs_qr_grouped(const ProbDesc* P, int count, int64_t max_n, cudaStream_t s);
+cudaError_t launch_runs_apply_w(int64_t n, int k, const double* V, const double* tau, const int* runs,
+                                const DevStatus* st, double* W, int64_t ldw, int64_t ncols, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_runs_apply_w_grouped(const ProbDesc* P, int count, int num_sms, cudaStream_t s);
+cudaError_t launch_runs_rotate_q_grouped(const ProbDesc* P, int count, int num_sms, cudaStream_t s);
 // Prefix sums of n_keep and n_defl over a class (one small kernel).
 cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStream_t s);
 // Grouped secular stages for one class (pole counts, zero finder, assembly).

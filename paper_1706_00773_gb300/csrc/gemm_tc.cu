@@ -481,8 +481,9 @@ __global__ void rowmax_grouped_kernel(const ProbDesc* __restrict__ P, int count,
   if (i >= n) return;
   const int cols_per = (n + gridDim.y - 1) / gridDim.y;
   const int j0 = blockIdx.y * cols_per, j1 = min(n, j0 + cols_per);
+  const double* Qsrc = d.st->n_runs ? d.Xout : d.Q;  // Xout holds Q~ = Q B when lam has runs
   double m = 0.0;
-  for (int j = j0; j < j1; ++j) m = fmax(m, fabs(d.Q[(size_t)j * n + i]));
+  for (int j = j0; j < j1; ++j) m = fmax(m, fabs(Qsrc[(size_t)j * n + i]));
   if (j1 > j0) atomicMax(&d.rmax[i], (unsigned long long)__double_as_longlong(m));
 }
 
@@ -499,6 +500,7 @@ __global__ void slice_q_grouped_kernel(const ProbDesc* __restrict__ P, int count
   const int lds = (n + 63) / 64 * 64;
   const size_t plane = (size_t)lds * (size_t)n;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const double* Qsrc = d.st->n_runs ? d.Xout : d.Q;  // Xout holds Q~ = Q B when lam has runs
   // The thread's row is fixed: its scale is formed once (one FMA per entry left).
   const int irow = i0 + tx;
   int erow_i = 0;
@@ -511,7 +513,7 @@ __global__ void slice_q_grouped_kernel(const ProbDesc* __restrict__ P, int count
     const int i = irow, j = j0 + jj;
     __nv_bfloat16 dd[kSlices];
     if (i < n && j < n) {
-      tc_split_prescaled(d.Q[(size_t)j * n + i], s40, dd);
+      tc_split_prescaled(Qsrc[(size_t)j * n + i], s40, dd);
       if (j == 0) d.erow[i] = erow_i;
     } else {
 #pragma unroll

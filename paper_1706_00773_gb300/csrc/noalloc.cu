@@ -10,7 +10,7 @@
 // one file-scope device array of fixed size, so nothing is allocated per call.
 //
 // Costs and rules of that choice:
-//   - every GPU that loads this library holds kStaticBytes (3 MiB) of device
+//   - every GPU that loads this library holds kStaticBytes (6 MiB) of device
 //     memory for the array until the process exits;
 //   - problems larger than EIG_STATIC_MAX_N (or k > EIG_MAX_K) are rejected with
 //     EIG_ETOOBIG;
@@ -32,7 +32,7 @@ using namespace eig;
 
 namespace {
 
-constexpr size_t kStaticBytes = size_t(3) << 20;
+constexpr size_t kStaticBytes = size_t(6) << 20;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_eig_scratch[kStaticBytes];
@@ -49,7 +49,8 @@ constexpr size_t scratch_bytes(size_t ld, size_t K) {
          al(8 * ld * K) /*Us*/ + al(4 * ld) /*idx_keep*/ + al(4 * ld) /*idx_defl*/ +
          al(8 * ld) /*lam_defl*/ + al(4 * ld) /*pole_cnt*/ + al(4 * ld) /*origin*/ +
          al(8 * ld) /*tau*/ + al(4 * ld) /*iters*/ + al(4 * ld) /*flags*/ + al(8 * ld * K) /*alpha*/ +
-         al(16 * ld) /*beta*/ + al(8 * ld) /*sidx*/ + al(8 * ld) /*mu_sec*/;
+         al(16 * ld) /*beta*/ + al(8 * ld) /*sidx*/ + al(8 * ld) /*mu_sec*/ +
+         2 * al(8 * ld * K) /*U copy, run reflectors*/ + al(8 * ld) /*their scalars*/ + al(4 * ld) /*runs*/;
 }
 static_assert(scratch_bytes(EIG_STATIC_MAX_N, EIG_MAX_K) <= kStaticBytes,
               "static scratch too small for EIG_STATIC_MAX_N");
@@ -134,12 +135,19 @@ extern "C" int eig_secular_values_static(int64_t n, int32_t k, const double* lam
   ro.beta = reinterpret_cast<double*>(take(16 * ld));
   ro.sidx = reinterpret_cast<int*>(take(8 * ld));
   double* mu_sec = reinterpret_cast<double*>(take(8 * ld));
+  double* Ur = reinterpret_cast<double*>(take(8 * ld * K));
+  double* Vr = reinterpret_cast<double*>(take(8 * ld * K));
+  double* taur = reinterpret_cast<double*>(take(8 * ld));
+  int* runs = reinterpret_cast<int*>(take(4 * ld));
   if (off > kStaticBytes) return EIG_ETOOBIG;  // cannot happen (static_assert above)
 
   // The array keeps the last call's contents: clear what must start at zero.
   CKS(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
   CKS(cudaMemsetAsync(counter, 0, sizeof(int), s));
-  CKS(launch_deflate(n, k, K, lambda, U, negmask, lam_keep, Us, (int)ld, idx_keep, idx_defl,
+  // runs of equal lambda are rotated in a copy of U (the caller's U is input only)
+  CKS(cudaMemcpyAsync(Ur, U, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+  CKS(launch_runs_qr(n, k, lambda, Ur, Vr, taur, runs, st, s));
+  CKS(launch_deflate(n, k, K, lambda, Ur, negmask, lam_keep, Us, (int)ld, idx_keep, idx_defl,
                      lam_defl, st, s));
   Sub sub;
   sub.n_dev = &st->n_keep;
