@@ -322,8 +322,9 @@ int eig_perturbation(eig_handle h, int64_t n, int32_t k, const double* Q, const 
    eigenvalues lie in [vl, vu), without the others.  Two counts give the
    secular roots in the interval, the zero finder solves only those (pole
    counts only at the poles around the interval), deflated pairs in the
-   interval are merged in, and X = Q W_sel (n x m) uses the FP64 GEMM in both
-   modes.  Q, lambda, K are read, not modified.
+   interval are merged in, and X = Q W_sel (n x m) is formed like the full
+   update's X: the FP64 GEMM in EIG_FP64, split-BF16 tensor-core products in
+   EIG_MIXED.  Q, lambda, K are read, not modified.
    Q (device n x n), lambda (device n, ascending), K (device n x k), all
    column-major; sigma host k entries or NULL.  mu (device max_m) receives the
    m selected eigenvalues, ascending; X (device n x max_m, column-major, may

@@ -972,7 +972,15 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   const size_t base = align_up(plan(nullptr, n, k, false, false, false).bytes, 256);
   // FP32 copies for the mixed-mode zero finder, then W_sel
   const size_t f32_bytes = mixed ? align_up(sizeof(float2) * ld, 256) + align_up(sizeof(float) * ld * Kp, 256) : 0;
-  const size_t need = base + 256 + f32_bytes + (X ? sizeof(double) * (size_t)n * (cap > 0 ? cap : 1) : 0);
+  const size_t wsel_bytes = X ? align_up(sizeof(double) * (size_t)n * (cap > 0 ? cap : 1), 256) : 0;
+  // mixed mode: X_sel = Q W_sel as split-BF16 products on the tensor cores
+  // (slices of Q and of W_sel's columns, row and column exponents)
+  const bool tc = mixed && X;
+  const size_t capc = cap > 0 ? cap : 1;
+  const size_t qs_bytes = tc ? align_up(2 * (size_t)tc_num_slices() * tc_slice_plane((int)n), 256) : 0;
+  const size_t ws_bytes = tc ? align_up(2 * (size_t)tc_num_slices() * (size_t)tc_slice_ld((int)n) * capc, 256) : 0;
+  const size_t aux_bytes = tc ? align_up(8 * (size_t)n, 256) + align_up(4 * (size_t)n, 256) + align_up(4 * capc, 256) : 0;
+  const size_t need = base + 256 + f32_bytes + wsel_bytes + qs_bytes + ws_bytes + aux_bytes;
   int rc = ensure_ws(h, need);
   if (rc) return rc;
   Carve c = plan(h->ws, n, k, false, false, false);
@@ -981,6 +989,14 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   float2* lamf = mixed ? reinterpret_cast<float2*>(h->ws + base + 256) : nullptr;
   float* Usf = mixed ? reinterpret_cast<float*>(h->ws + base + 256 + align_up(sizeof(float2) * ld, 256)) : nullptr;
   double* Wsel = X ? reinterpret_cast<double*>(h->ws + base + 256 + f32_bytes) : nullptr;
+  char* tcb = h->ws + base + 256 + f32_bytes + wsel_bytes;
+  __nv_bfloat16* Qs = tc ? reinterpret_cast<__nv_bfloat16*>(tcb) : nullptr;
+  __nv_bfloat16* Ws = tc ? reinterpret_cast<__nv_bfloat16*>(tcb + qs_bytes) : nullptr;
+  unsigned long long* rmax = tc ? reinterpret_cast<unsigned long long*>(tcb + qs_bytes + ws_bytes) : nullptr;
+  int* erow = tc ? reinterpret_cast<int*>(tcb + qs_bytes + ws_bytes + align_up(8 * (size_t)n, 256)) : nullptr;
+  int* fcol = tc ? reinterpret_cast<int*>(tcb + qs_bytes + ws_bytes + align_up(8 * (size_t)n, 256) +
+                                          align_up(4 * (size_t)n, 256))
+                 : nullptr;
   const double xv[2] = {vl, vu};
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
@@ -1031,7 +1047,13 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   CK(launch_assemble_select(sub, ro, n, c.idx_defl, c.lam_defl, dlo, dsel, r0, r1, c.mu_sec, mu, Wsel, s));
   if (X) {
     CK(launch_runs_apply_w(n, k, c.Vr, c.taur, c.runs, c.st, Wsel, n, m, h->num_sms, s));  // W_sel <- B W_sel
-    CK(launch_gemm_f64(n, m, n, Q, n, Wsel, n, X, n, s));
+    if (tc) {
+      CK(launch_slice_q((int)n, Q, rmax, erow, Qs, c.st, s));
+      CK(launch_slice_cols((int)n, (int)m, Wsel, fcol, Ws, s));
+      CK(launch_gemm_tc((int)n, Qs, Ws, erow, fcol, X, (int)n, c.st, &c.st->flags, s, (int)m));
+    } else {
+      CK(launch_gemm_f64(n, m, n, Q, n, Wsel, n, X, n, s));
+    }
   }
   CK(cudaMemcpyAsync(h->st_host, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

@@ -331,11 +331,15 @@ int tc_num_slices();
 // Row exponents and slices of Q (column-major FP64).  rmax: n u64 scratch.
 cudaError_t launch_slice_q(int n, const double* Q, unsigned long long* rmax, int* erow,
                            __nv_bfloat16* Qs, const DevStatus* st, cudaStream_t s);
-// X (column-major, ldx) = 2^(e_i+f_r-16) sum_{p+q<=6} Qs_p Ws_q^T.  err: status word
-// that receives ST_TIMEOUT if a bounded wait gave up.
+// Column exponents f_r and slices of the m columns of a column-major n x m W
+// (as rows of W^T: Ws holds tc_num_slices() planes of m x tc_slice_ld(n)).
+cudaError_t launch_slice_cols(int n, int m, const double* W, int* fcol, __nv_bfloat16* Ws, cudaStream_t s);
+// X (column-major, ldx; n x ncols) = 2^(e_i+f_r-16) sum_{p+q<=6} Qs_p Ws_q^T,
+// ncols = n when negative.  err: status word that receives ST_TIMEOUT if a
+// bounded wait gave up.
 cudaError_t launch_gemm_tc(int n, const __nv_bfloat16* Qs, const __nv_bfloat16* Ws, const int* erow,
                            const int* fcol, double* X, int ldx, const DevStatus* st, int* err,
-                           cudaStream_t s);
+                           cudaStream_t s, int ncols = -1);
 // Grouped versions over a table of updates.  Host-side prefix arrays (count+1)
 // of per-update work: row blocks of 256 (rowmax), 32x32 slice tiles, 128x128
 // GEMM tiles.  maps: device array of 2*count tensor maps (Q slices, W slices)

@@ -157,7 +157,8 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 }
 
 struct GemmArgs {
-  int n;           // X, Q, W are n x n
+  int n;           // rows of X and Q; the contraction length
+  int ncols;       // columns of X and W (n for the full update)
   int ldx;         // leading dimension of X (column-major)
   double* X;
   const int* erow;  // e_i
@@ -368,7 +369,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
 #pragma unroll
         for (int c = 0; c < 64; ++c) {
           const int col = n0 + half * 64 + c;
-          if (col < a.n) {
+          if (col < a.ncols) {
             const double x = (double)hi[c] + (double)lo[c];
             a.X[(size_t)col * a.ldx + row] = ldexp(x, er + a.fcol[col] - 16);
           }
@@ -411,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   GemmArgs a;
   a.n = d.n;
+  a.ncols = d.n;
   a.ldx = d.n;
   a.X = d.Xout;
   a.erow = d.erow;
@@ -532,9 +534,45 @@ __global__ void slice_q_grouped_kernel(const ProbDesc* __restrict__ P, int count
   }
 }
 
+// Columns of a column-major n x m matrix W -> slices Ws[q][r][j] of W^T (row r =
+// column r of W, j contiguous, leading dim lds), each with its own exponent
+// f_r (one CTA per column: max |W[:, r]|, then the split).
+constexpr int kRowThreads = 256;
+__global__ void __launch_bounds__(kRowThreads) slice_cols_kernel(int n, const double* __restrict__ W,
+                                                                 int* __restrict__ fcol,
+                                                                 __nv_bfloat16* __restrict__ Ws, size_t plane,
+                                                                 int lds) {
+  __shared__ double sh[kRowThreads / 32];
+  const int r = blockIdx.x;
+  const double* w = W + (size_t)r * n;
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += kRowThreads) mx = fmax(mx, fabs(w[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < kRowThreads / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) sh[0] = mx;
+  }
+  __syncthreads();
+  const int f = tc_scale_exp(sh[0]);
+  if (threadIdx.x == 0) fcol[r] = f;
+  const double s40 = ldexp(1.0, 40 - f);
+  for (int j = threadIdx.x; j < n; j += kRowThreads) {
+    __nv_bfloat16 d[kSlices];
+    tc_split_prescaled(w[j], s40, d);
+#pragma unroll
+    for (int q = 0; q < kSlices; ++q) Ws[(size_t)q * plane + (size_t)r * lds + j] = d[q];
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-int make_map(CUtensorMap* map, const void* base, int n, int lds) {
+// Map of a slice stack: kSlices planes of `rows` rows of n BF16 (leading dim lds).
+int make_map(CUtensorMap* map, const void* base, int n, int lds, int rows) {
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -544,8 +582,8 @@ int make_map(CUtensorMap* map, const void* base, int n, int lds) {
       return -1;
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)kSlices};
-  cuuint64_t strides[2] = {(cuuint64_t)lds * 2, (cuuint64_t)lds * 2 * (cuuint64_t)n};
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)rows, (cuuint64_t)kSlices};
+  cuuint64_t strides[2] = {(cuuint64_t)lds * 2, (cuuint64_t)lds * 2 * (cuuint64_t)rows};
   cuuint32_t box[3] = {BK, 128, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
@@ -572,8 +610,14 @@ cudaError_t launch_slice_q(int n, const double* Q, unsigned long long* rmax, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_slice_cols(int n, int m, const double* W, int* fcol, __nv_bfloat16* Ws, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  slice_cols_kernel<<<m, kRowThreads, 0, s>>>(n, W, fcol, Ws, (size_t)tc_slice_ld(n) * (size_t)m, tc_slice_ld(n));
+  return cudaGetLastError();
+}
+
 int tc_encode_map(void* map64, const void* base, int n) {
-  return make_map(reinterpret_cast<CUtensorMap*>(map64), base, n, tc_slice_ld(n));
+  return make_map(reinterpret_cast<CUtensorMap*>(map64), base, n, tc_slice_ld(n), n);
 }
 
 cudaError_t launch_slice_q_grouped(const ProbDesc* P, int count, const int* rb_prefix, int total_rb,
@@ -595,15 +639,18 @@ cudaError_t launch_gemm_tc_grouped(const ProbDesc* P, int count, const void* map
 
 cudaError_t launch_gemm_tc(int n, const __nv_bfloat16* Qs, const __nv_bfloat16* Ws, const int* erow,
                            const int* fcol, double* X, int ldx, const DevStatus* st, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, int ncols) {
+  if (ncols < 0) ncols = n;
+  if (ncols == 0) return cudaSuccess;
   CUtensorMap mq, mw;
   const int lds = tc_slice_ld(n);
-  if (make_map(&mq, Qs, n, lds) != 0 || make_map(&mw, Ws, n, lds) != 0) return cudaErrorInvalidValue;
+  if (make_map(&mq, Qs, n, lds, n) != 0 || make_map(&mw, Ws, n, lds, ncols) != 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmemBytes);
   if (e != cudaSuccess) return e;
   GemmArgs a;
   a.n = n;
+  a.ncols = ncols;
   a.ldx = ldx;
   a.X = X;
   a.erow = erow;
@@ -611,7 +658,7 @@ cudaError_t launch_gemm_tc(int n, const __nv_bfloat16* Qs, const __nv_bfloat16* 
   a.st = st;
   a.err = err;
   a.tiles_m = (n + BM - 1) / BM;
-  a.tiles_n = (n + BN - 1) / BN;
+  a.tiles_n = (ncols + BN - 1) / BN;
   gemm_tc_kernel<<<a.tiles_m * a.tiles_n, kThreads, kSmemBytes, s>>>(mq, mw, a);
   return cudaGetLastError();
 }
