@@ -172,12 +172,32 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
  *                           synchronous.
  * what = EIG_Q_WORKSPACE:   in = const eig_problem*, out = uint64_t* bytes the
  *                           handle needs for that problem.
+ * what = EIG_Q_METRICS:     in = NULL, out = eig_metrics*: the handle's
+ *                           counters since eig_update_init (host-side, no
+ *                           device synchronisation; batch tickets still running
+ *                           count as pending).
  * out_bytes is the size of *out; EIG_EINVAL if too small. */
 #define EIG_Q_STATUS 1
 #define EIG_Q_REPORT 2
 #define EIG_Q_LAST_STATUS 3
 #define EIG_Q_COUNT 4
 #define EIG_Q_WORKSPACE 5
+#define EIG_Q_METRICS 6
+
+typedef struct {
+  int64_t calls;            /* eig_update_rank_k and eig_update_batch calls */
+  int64_t updates;          /* problems submitted (each problem of a batch) */
+  int64_t eigenpairs;       /* sum of n over the problems submitted */
+  int64_t updates_ok;       /* finished with EIG_OK */
+  int64_t updates_failed;   /* finished or rejected with an error status
+                               (EIG_ENOTCONV included) */
+  int64_t updates_pending;  /* submitted, final status not read yet (an
+                               EIG_ASYNC update stays here when another
+                               update starts before EIG_Q_LAST_STATUS) */
+  int64_t launches;         /* kernels launched by the update paths */
+  int64_t workspace_allocs; /* workspace (re)allocations */
+  uint64_t workspace_bytes; /* current workspace size */
+} eig_metrics;
 
 typedef struct {
   int64_t n;             /* size of the (already projected) problem */

@@ -19,7 +19,7 @@ __all__ = [
     "EIG_OK", "EIG_EINVAL", "EIG_ENOMEM", "EIG_ENOTCONV", "EIG_ETIMEOUT", "EIG_ECUDA",
     "EIG_ENOTSUP", "EIG_EBUSY", "EIG_FP64", "EIG_MIXED", "EIG_VALUES", "EIG_VECTORS",
     "EIG_REPORT", "EIG_ASYNC", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT", "EIG_Q_LAST_STATUS",
-    "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EigError", "lib", "library_path", "colmajor",
+    "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EIG_Q_METRICS", "EigError", "lib", "library_path", "colmajor",
     "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
     "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
@@ -34,7 +34,7 @@ EIG_STATIC_MAX_N = 8192
 EIG_MAX_K = 16
 EIG_FP64, EIG_MIXED = 0, 1
 EIG_VALUES, EIG_VECTORS, EIG_REPORT, EIG_ASYNC = 1, 2, 4, 8
-EIG_Q_STATUS, EIG_Q_REPORT, EIG_Q_LAST_STATUS, EIG_Q_COUNT, EIG_Q_WORKSPACE = 1, 2, 3, 4, 5
+EIG_Q_STATUS, EIG_Q_REPORT, EIG_Q_LAST_STATUS, EIG_Q_COUNT, EIG_Q_WORKSPACE, EIG_Q_METRICS = 1, 2, 3, 4, 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libeigupdate.so")
@@ -60,6 +60,16 @@ class eig_problem(ctypes.Structure):
                 ("Q", ctypes.c_void_p), ("lambda_", ctypes.c_void_p), ("K", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("Q_out", ctypes.c_void_p), ("want", ctypes.c_uint32),
                 ("pad2_", ctypes.c_uint32)]
+
+
+class eig_metrics(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("updates", ctypes.c_int64), ("eigenpairs", ctypes.c_int64),
+                ("updates_ok", ctypes.c_int64), ("updates_failed", ctypes.c_int64),
+                ("updates_pending", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("workspace_allocs", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class eig_report(ctypes.Structure):
@@ -267,6 +277,10 @@ def eig_update_query(h, what: int, ticket: int | None = None):
     if what == EIG_Q_LAST_STATUS:
         out = ctypes.c_int32()
         return L.eig_update_query(h, what, None, ctypes.byref(out), ctypes.sizeof(out))
+    if what == EIG_Q_METRICS:
+        m = eig_metrics()
+        _check(L.eig_update_query(h, what, None, ctypes.byref(m), ctypes.sizeof(m)), "eig_update_query(METRICS)")
+        return m.as_dict()
     raise ValueError("use eig_count / workspace_bytes for this query")
 
 

@@ -157,6 +157,10 @@ struct eig_ctx {
   cudaStream_t last_stream = nullptr;
   int last_launches = 0;
   bool last_pending = false;
+  bool last_counted = true;  // the last rank_k call's outcome is in the metrics
+  // EIG_Q_METRICS counters (batch tickets are resolved when queried)
+  int64_t m_calls = 0, m_updates = 0, m_pairs = 0, m_ok = 0, m_failed = 0, m_launches = 0, m_allocs = 0;
+  int64_t m_unread = 0;  // EIG_ASYNC updates superseded before their status was read
   std::mutex mu;
   std::vector<Ticket> tickets;
 };
@@ -180,6 +184,7 @@ int ensure_ws(eig_ctx* h, size_t bytes) {
   }
   h->ws = static_cast<char*>(p);
   h->ws_bytes = bytes;
+  ++h->m_allocs;
   return EIG_OK;
 }
 
@@ -625,12 +630,50 @@ int eig_update_destroy(eig_handle h) {
   return EIG_OK;
 }
 
+// Outcome of a synchronous (or synchronised) update in the handle's counters.
+static void count_outcome(eig_ctx* h, int status) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (status == EIG_OK) ++h->m_ok;
+  else ++h->m_failed;
+}
+
+static int update_one(eig_ctx* h, eig_problem* P, unsigned long long negmask, int kplus, eig_report* rep,
+                      void* stream);
+
 int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* stream) {
   if (!h) return EIG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    ++h->m_calls;
+    ++h->m_updates;
+    if (P && P->n > 0) h->m_pairs += P->n;
+  }
   unsigned long long negmask = 0;
   int kplus = 0;
   int rc = validate(P, &negmask, &kplus);
-  if (rc) return rc;
+  if (rc) {
+    count_outcome(h, rc);
+    return rc;
+  }
+  rc = update_one(h, P, negmask, kplus, rep, stream);
+  if (h->last_counted) return rc;
+  if (!h->last_pending) {  // finished (or failed before its status copy)
+    h->last_counted = true;
+    count_outcome(h, rc);
+  }
+  return rc;
+}
+
+// The work of eig_update_rank_k after validation.
+static int update_one(eig_ctx* h, eig_problem* P, unsigned long long negmask, int kplus, eig_report* rep,
+                      void* stream) {
+  int rc = EIG_OK;
+  if (!h->last_counted) {  // an EIG_ASYNC update whose status nobody read
+    std::lock_guard<std::mutex> lk(h->mu);
+    ++h->m_unread;
+  }
+  h->last_counted = false;
+  h->last_pending = false;
   DeviceGuard g(h->device);
   if (!g.ok) return EIG_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -647,6 +690,10 @@ int eig_update_rank_k(eig_handle h, eig_problem* P, eig_report* rep, void* strea
   rc = enqueue_table(h, T, 1, vectors, mixed, report, s, rep ? h->ev : nullptr, &h->last_launches, img, P,
                      negmask);
   if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->m_launches += h->last_launches;
+  }
   h->last_stream = s;
   CK(cudaMemcpyAsync(h->st_host, T.d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   if (P->want & EIG_ASYNC) {
@@ -707,6 +754,10 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
   size_t need = 0;
   for (int v = 0; v < 2; ++v)
     if (!tab[v].empty()) need = std::max(need, layout_table(h, tab[v], nullptr, v == 1, mixed, nullptr).bytes);
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    ++h->m_calls;
+  }
   int rc = ensure_ws(h, need);
   if (rc) return rc;
   std::vector<Ticket> made(count);
@@ -730,6 +781,10 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
     int nl = 0;
     rc = enqueue_table(h, T, (int)tab[v].size(), v == 1, mixed, false, s, nullptr, &nl, img, nullptr, 0);
     if (rc) return rc;
+    {
+      std::lock_guard<std::mutex> lk(h->mu);
+      h->m_launches += nl;
+    }
     for (size_t j = 0; j < tab[v].size(); ++j)
       CK(cudaMemcpyAsync(made[slot[v][j]].host, T.d_st + j, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     // The next table reuses the workspace: keep the tables stream-ordered.
@@ -795,8 +850,49 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
         h->last_pending = false;
       }
       const int status = status_of(*h->st_host);
+      if (!h->last_counted) {
+        h->last_counted = true;
+        count_outcome(h, status);
+      }
       *static_cast<int32_t*>(out) = status;
       return status;
+    }
+    case EIG_Q_METRICS: {
+      if (!out || out_bytes < sizeof(eig_metrics)) return EIG_EINVAL;
+      eig_metrics m{};
+      std::lock_guard<std::mutex> lk(h->mu);
+      m.calls = h->m_calls;
+      m.updates = h->m_updates;
+      m.eigenpairs = h->m_pairs;
+      m.updates_ok = h->m_ok;
+      m.updates_failed = h->m_failed;
+      m.launches = h->m_launches;
+      m.workspace_allocs = h->m_allocs;
+      m.workspace_bytes = h->ws_bytes;
+      for (const Ticket& t : h->tickets) {  // batch problems: resolved now, without waiting
+        ++m.updates;
+        m.eigenpairs += t.n > 0 ? t.n : 0;
+        int status = t.pre_status;
+        if (status == EIG_OK) {
+          const cudaError_t q = cudaEventQuery(t.done);
+          if (q == cudaErrorNotReady) {
+            cudaGetLastError();
+            ++m.updates_pending;
+            continue;
+          }
+          if (q != cudaSuccess) {
+            cudaGetLastError();
+            status = EIG_ECUDA;
+          } else {
+            status = status_of(*t.host);
+          }
+        }
+        if (status == EIG_OK) ++m.updates_ok;
+        else ++m.updates_failed;
+      }
+      m.updates_pending += h->m_unread + (h->last_counted ? 0 : 1);
+      *static_cast<eig_metrics*>(out) = m;
+      return EIG_OK;
     }
     case EIG_Q_WORKSPACE: {
       const eig_problem* P = static_cast<const eig_problem*>(in);

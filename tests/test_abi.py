@@ -2,6 +2,7 @@
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -49,7 +50,7 @@ def test_constants_match_header():
     txt = open(HEADER).read()
     for name in ("EIG_OK", "EIG_EINVAL", "EIG_ENOMEM", "EIG_ENOTCONV", "EIG_ETIMEOUT", "EIG_ECUDA",
                  "EIG_ENOTSUP", "EIG_EBUSY", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT",
-                 "EIG_Q_LAST_STATUS", "EIG_Q_COUNT", "EIG_Q_WORKSPACE"):
+                 "EIG_Q_LAST_STATUS", "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EIG_Q_METRICS"):
         m = re.search(r"#define %s \(?(-?\d+)\)?" % name, txt)
         assert m, name
         assert getattr(eu, name) == int(m.group(1)), name
@@ -68,3 +69,32 @@ def test_init_without_gpu_fails_cleanly(built_lib):
     with pytest.raises(eu.EigError) as ei:
         eu.eig_update_init(0)
     assert ei.value.code == eu.EIG_ECUDA
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's size and field
+    offsets (a C program compiled against the header prints them)."""
+    import paper_1706_00773_gb300 as eu
+
+    structs = {name: getattr(eu, name) for name in ("eig_init_params", "eig_problem", "eig_report", "eig_metrics",
+                                                     "eig_count_args", "eig_server_params", "eig_request_info")}
+    renames = {"lambda_": "lambda"}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "eig_update.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            cf = renames.get(f, f)
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, cf))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), "-o", str(exe), str(src)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        a, b, c = ln.split()
+        got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
