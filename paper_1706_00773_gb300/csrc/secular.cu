@@ -438,6 +438,109 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
   }
 }
 
+// The same round-robin Jacobi in FP32, for the k x k work of a count whose
+// FP32 result is certified by an error bound (the rotations run on the FP32
+// pipe; GB300 issues FP64 at 1/64 of the FP32 rate).  Stops once the
+// off-diagonal mass is below 1e-14 of the diagonal's (FP32 resolution).
+template <int K>
+__device__ void warp_jacobi_f32(float* A, float* V, int lane) {
+  constexpr int KP = K + 1;
+  if (V) {
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int r = idx / K, c = idx - (idx / K) * K;
+      V[r * KP + c] = (r == c) ? 1.0f : 0.0f;
+    }
+  }
+  __syncwarp();
+  if constexpr (K == 1) return;
+  constexpr int M = (K + 1) / 2 * 2;
+  constexpr int P = M / 2;
+  constexpr int ITEMS = P * K;
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    float off = 0.0f, dia = 0.0f;
+    for (int idx = lane; idx < K * K; idx += 32) {
+      const int r = idx / K, c = idx - (idx / K) * K;
+      const float v = A[r * KP + c];
+      if (r != c) off = fmaf(v, v, off); else dia = fmaf(v, v, dia);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off == 0.0f || off <= 1e-14f * dia) break;
+    for (int rnd = 0; rnd < M - 1; ++rnd) {
+      int pj = 0, qj = 0;
+      float cj = 1.0f, sj = 0.0f;
+      bool act = false;
+      if (lane < P) {
+        int a, b;
+        if (lane == 0) {
+          a = rnd;
+          b = M - 1;
+        } else {
+          a = (rnd + lane) % (M - 1);
+          b = (rnd - lane + (M - 1)) % (M - 1);
+        }
+        pj = a < b ? a : b;
+        qj = a < b ? b : a;
+        if (qj < K) {
+          const float apq = A[pj * KP + qj], app = A[pj * KP + pj], aqq = A[qj * KP + qj];
+          if (apq != 0.0f) {
+            const float th = (aqq - app) / (2.0f * apq);
+            float t;
+            if (!(fabsf(th) <= 1e18f)) {
+              t = 0.5f / th;
+            } else {
+              t = 1.0f / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+              if (th < 0.0f) t = -t;
+            }
+            cj = rsqrtf(fmaf(t, t, 1.0f));
+            sj = t * cj;
+            act = true;
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int base = 0; base < ITEMS; base += 32) {
+        const int idx = base + lane;
+        const int jj = idx < ITEMS ? idx / K : 0;
+        const int r = idx - jj * K;
+        const int p = __shfl_sync(0xffffffffu, pj, jj), q = __shfl_sync(0xffffffffu, qj, jj);
+        const float c = __shfl_sync(0xffffffffu, cj, jj), sn = __shfl_sync(0xffffffffu, sj, jj);
+        const bool go = __shfl_sync(0xffffffffu, act ? 1 : 0, jj) != 0;
+        if (idx < ITEMS && go) {
+          const float arp = A[r * KP + p], arq = A[r * KP + q];
+          A[r * KP + p] = c * arp - sn * arq;
+          A[r * KP + q] = sn * arp + c * arq;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int base = 0; base < ITEMS; base += 32) {
+        const int idx = base + lane;
+        const int jj = idx < ITEMS ? idx / K : 0;
+        const int r = idx - jj * K;
+        const int p = __shfl_sync(0xffffffffu, pj, jj), q = __shfl_sync(0xffffffffu, qj, jj);
+        const float c = __shfl_sync(0xffffffffu, cj, jj), sn = __shfl_sync(0xffffffffu, sj, jj);
+        const bool go = __shfl_sync(0xffffffffu, act ? 1 : 0, jj) != 0;
+        if (idx < ITEMS && go) {
+          const float apr = A[p * KP + r], aqr = A[q * KP + r];
+          A[p * KP + r] = c * apr - sn * aqr;
+          A[q * KP + r] = sn * apr + c * aqr;
+          if (V) {
+            const float vrp = V[r * KP + p], vrq = V[r * KP + q];
+            V[r * KP + p] = c * vrp - sn * vrq;
+            V[r * KP + q] = sn * vrp + c * vrq;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __device__ __forceinline__ bool input_invalid(const DevStatus* st) {
   return (st->flags & (ST_UNSORTED | ST_NONFINITE)) != 0;
 }
@@ -453,6 +556,97 @@ __device__ __forceinline__ double sigma_of(unsigned long long negmask, int a) {
 //   #{lam_i < x} + dim R + #{positive eigenvalues of (Sigma - M~(x)) on R^perp} - k_plus
 // with M~ the sum over the other terms.  Away from poles G = 0 and this is (1).
 // ----------------------------------------------------------------------------
+// The k x k part of a count at pole q from FP32 sums (M~ in M, S1 and S2 in
+// s_err), on the FP32 pipe: the range R of G = u_q u_q^T (FP32 Jacobi on G
+// scaled by 1/max|u_q|^2), T = V^T (Sigma - M~) V with R decoupled, and T's
+// eigenvalues.  The count is kept only when every eigenvalue on R^perp clears
+//   E = 1.25 ((L + 8) 2^-24 S1 + 2^-46 max|lam| S2) + 64 K 2^-24 |B|_F,
+// the FP32 error of the sums plus that of the FP32 k x k work (B's rounding,
+// the products V^T B V, R's leakage into R^perp, the Jacobi's rotations);
+// otherwise *s_redo asks for the FP64 pass.
+template <int K>
+__device__ void count_tail_f32(const Sub& sub, int n, int pole, const double* M, double* Gm, double* Vg,
+                               double* Ev, const double* s_err, int* out, int* s_redo, int lane) {
+  constexpr int KP = K + 1;
+  float* Gf = reinterpret_cast<float*>(Gm);   // K x KP
+  float* Bf = Gf + K * KP;                    // K x KP (Gm holds 2 K KP floats)
+  float* Vf = reinterpret_cast<float*>(Vg);   // K x KP
+  float* Evf = reinterpret_cast<float*>(Ev);  // K
+  const double S1 = s_err[0], S2 = s_err[1];
+  float umax = 0.0f;
+  for (int r = 0; r < K; ++r) umax = fmaxf(umax, fabsf(sub.Usf[(size_t)r * sub.ld + pole]));
+  // 1/0 in FP32 (a repeated pole) or a row below FP32's normal range: FP64 pass.
+  if (!(S1 < INFINITY) || !(S2 < INFINITY) || !(umax >= 0x1p-60f)) {
+    if (lane == 0) *s_redo = 1;
+    __syncwarp();
+    return;
+  }
+  const float us = 1.0f / umax;
+  float bsq = 0.0f;
+  for (int idx = lane; idx < K * K; idx += 32) {
+    const int r = idx / K, c = idx - (idx / K) * K;
+    const float b = (float)((r == c ? sigma_of(sub.negmask, r) : 0.0) - M[r * KP + c]);
+    Bf[r * KP + c] = b;
+    bsq = fmaf(b, b, bsq);
+    Gf[r * KP + c] = (sub.Usf[(size_t)r * sub.ld + pole] * us) * (sub.Usf[(size_t)c * sub.ld + pole] * us);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bsq += __shfl_xor_sync(0xffffffffu, bsq, o);
+  __syncwarp();
+  warp_jacobi_f32<K>(Gf, Vf, lane);
+  if (lane < K) Evf[lane] = Gf[lane * KP + lane];
+  __syncwarp();
+  float emax = 0.0f;
+  for (int j = 0; j < K; ++j) emax = fmaxf(emax, Evf[j]);
+  const float tol = 64.0f * 0x1p-24f * (float)K * emax;
+  int dimR = 0;
+  for (int j = 0; j < K; ++j) dimR += (Evf[j] > tol) ? 1 : 0;
+  // T = V^T B V into Gf: lane j forms column j.
+  float bv[K];
+  if (lane < K) {
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+      float acc = 0.0f;
+      for (int q = 0; q < K; ++q) acc = fmaf(Bf[r * KP + q], Vf[q * KP + lane], acc);
+      bv[r] = acc;
+    }
+  }
+  __syncwarp();
+  if (lane < K) {
+    for (int i = 0; i < K; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int r = 0; r < K; ++r) acc = fmaf(Vf[r * KP + i], bv[r], acc);
+      Gf[i * KP + lane] = acc;
+    }
+  }
+  __syncwarp();
+  const bool rng = lane < K && Evf[lane] > tol;  // range directions: diagonal -1, never counted
+  if (rng) {
+    for (int i = 0; i < K; ++i) {
+      Gf[lane * KP + i] = 0.0f;
+      Gf[i * KP + lane] = 0.0f;
+    }
+  }
+  __syncwarp();
+  if (rng) Gf[lane * KP + lane] = -1.0f;
+  __syncwarp();
+  warp_jacobi_f32<K>(Gf, nullptr, lane);
+  const float v = (lane < K) ? Gf[lane * KP + lane] : 0.0f;
+  const unsigned pos = __ballot_sync(0xffffffffu, lane < K && v > 0.0f);
+  const int cnt = pole + dimR + __popc(pos) - sub.kplus;
+  const double L = (double)((n + 31) / 32);
+  const double Eb = 1.25 * ((L + 8.0) * 0x1p-24 * S1 + 0x1p-46 * sub.st->lam_absmax * S2) +
+                    64.0 * K * 0x1p-24 * sqrt((double)bsq);
+  const bool okj = lane >= K || rng || fabs((double)v) > 2.0 * Eb;
+  const bool ok = __all_sync(0xffffffffu, okj) && (Eb < INFINITY);
+  if (lane == 0) {
+    if (ok) *out = cnt;
+    *s_redo = ok ? 0 : 1;
+  }
+  __syncwarp();
+}
+
 template <int K>
 __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, bool absolute,
                                             double tau, double lam_o, int pole, int* out, double* M0,
@@ -460,11 +654,11 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
                                             int g, int e, int lane) {
   constexpr int E = warps_per_root(K);
   constexpr int KP = K + 1;
-  // At a pole with FP32 copies present, a first pass sums M~ in FP32 (the
-  // pole's own term u_q u_q^T exactly in FP64 as G, #{lam_i < lam_q} = q);
-  // a count that the error bound cannot certify is taken again in FP64.  A
-  // repeated or nearly repeated pole gives 1/0 in FP32, an infinite bound,
-  // and so the FP64 pass.
+  // At a pole with FP32 copies present, a first pass sums M~ in FP32 and does
+  // the k x k work in FP32 too (count_tail_f32, #{lam_i < lam_q} = q); a count
+  // that the error bound cannot certify is taken again in FP64.  A repeated
+  // or nearly repeated pole gives 1/0 in FP32, an infinite bound, and so the
+  // FP64 pass.
   const bool try32 = !absolute && sub.lamf != nullptr;
   for (int pass = try32 ? 0 : 1; pass < 2; ++pass) {
     const bool p32 = (pass == 0);
@@ -481,22 +675,15 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
       }
     }
     group_sync<E>(g);
-    if (active && e == 0) {
-      if (p32) {
-        below = pole;
-        for (int idx = lane; idx < K * K; idx += 32) {
-          const int r = idx / K, c = idx - (idx / K) * K;
-          Gm[r * KP + c] = sub.Us[(size_t)r * sub.ld + pole] * sub.Us[(size_t)c * sub.ld + pole];
-        }
-        __syncwarp();
-      }
+    if (active && e == 0 && p32) {
+      count_tail_f32<K>(sub, n, pole, M, Gm, Vg, Ev, s_err, out, s_redo, lane);
+    } else if (active && e == 0) {
       for (int idx = lane; idx < K * K; idx += 32) {
         const int r = idx / K, c = idx - (idx / K) * K;
         const double v = -M[r * KP + c];
         M[r * KP + c] = (r == c) ? v + sigma_of(sub.negmask, r) : v;
       }
       double gmax = 0.0;
-      double tol_rng = INFINITY;
       for (int idx = lane; idx < K * K; idx += 32) {
         const int r = idx / K, c = idx - (idx / K) * K;
         gmax = fmax(gmax, fabs(Gm[r * KP + c]));
@@ -514,7 +701,6 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
         double emax = 0.0;
         for (int j = 0; j < K; ++j) emax = fmax(emax, Ev[j]);
         const double tol = 64.0 * kEps * K * emax;
-        tol_rng = tol;
         for (int j = 0; j < K; ++j) dimR += (Ev[j] > tol) ? 1 : 0;
         // T = V^T B V into Gm: lane j forms column j.
         double bv[K];
@@ -553,24 +739,9 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
       }
       const unsigned pos = __ballot_sync(0xffffffffu, lane < K && M[(lane < K ? lane : 0) * KP + (lane < K ? lane : 0)] > 0.0);
       const int cnt = below + dimR + __popc(pos) - sub.kplus;
-      bool ok = true;
-      if (p32) {
-        // Certify: each eigenvalue on R^perp must clear the FP32 error of M~
-        // (Weyl; V is orthogonal), E = (L + 8) 2^-24 S1 + 2^-46 max|lam| S2.
-        const bool rng = lane < K && gmax > 0.0 && Ev[lane] > tol_rng;
-        const double v = (lane < K) ? M[lane * KP + lane] : 0.0;
-        double vmax = (lane < K && !rng) ? fabs(v) : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-        const double L = (double)((n + 31) / 32);
-        const double Eb = 1.25 * ((L + 8.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
-                          64.0 * kEps * vmax;
-        const bool okj = lane >= K || rng || fabs(v) > 2.0 * Eb;
-        ok = __all_sync(0xffffffffu, okj) && (Eb < INFINITY) && isfinite(vmax);
-      }
       if (lane == 0) {
-        if (ok) *out = cnt;
-        *s_redo = ok ? 0 : 1;
+        *out = cnt;
+        *s_redo = 0;
       }
       __syncwarp();
         }
