@@ -61,6 +61,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// FP32 butterfly: the sums taken in FP32 are also reduced across the warp in
+// FP32 (five more roundings per sum, in the error bounds' L + 16; every lane
+// ends with the same value).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 template <int E>
 __device__ __forceinline__ void group_sync(int g) {
   if (E == 1) {
@@ -161,7 +170,8 @@ __device__ __forceinline__ int accumulate(const double* __restrict__ lam,
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     A[s] = warp_sum(A[s]);
-    B64[s] = (MODE != ACC_M) ? warp_sum((double)B[s]) : 0.0;
+    if (MODE == ACC_MN32) B64[s] = (double)warp_sum_f((float)B[s]);
+    else B64[s] = (MODE != ACC_M) ? warp_sum((double)B[s]) : 0.0;
   }
   if (MODE == ACC_MG) below = __reduce_add_sync(0xffffffffu, below);
   if (lane == 0) {
@@ -263,10 +273,10 @@ __device__ __forceinline__ void accumulate32(const float2* __restrict__ lamf, co
   double A64[NS], B64[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    A64[s] = warp_sum((double)A[s]);
-    B64[s] = WN ? warp_sum((double)B[s]) : 0.0;
+    A64[s] = (double)warp_sum_f(A[s]);
+    B64[s] = WN ? (double)warp_sum_f(B[s]) : 0.0;
   }
-  const double S1 = warp_sum((double)s1), S2 = warp_sum((double)s2);
+  const double S1 = (double)warp_sum_f(s1), S2 = (double)warp_sum_f(s2);
   if (lane == 0) {
     int s = 0;
 #pragma unroll
@@ -560,7 +570,7 @@ __device__ __forceinline__ double sigma_of(unsigned long long negmask, int a) {
 // s_err), on the FP32 pipe: the range R of G = u_q u_q^T (FP32 Jacobi on G
 // scaled by 1/max|u_q|^2), T = V^T (Sigma - M~) V with R decoupled, and T's
 // eigenvalues.  The count is kept only when every eigenvalue on R^perp clears
-//   E = 1.25 ((L + 8) 2^-24 S1 + 2^-46 max|lam| S2) + 64 K 2^-24 |B|_F,
+//   E = 1.25 ((L + 16) 2^-24 S1 + 2^-46 max|lam| S2) + 64 K 2^-24 |B|_F,
 // the FP32 error of the sums plus that of the FP32 k x k work (B's rounding,
 // the products V^T B V, R's leakage into R^perp, the Jacobi's rotations);
 // otherwise *s_redo asks for the FP64 pass.
@@ -636,7 +646,7 @@ __device__ void count_tail_f32(const Sub& sub, int n, int pole, const double* M,
   const unsigned pos = __ballot_sync(0xffffffffu, lane < K && v > 0.0f);
   const int cnt = pole + dimR + __popc(pos) - sub.kplus;
   const double L = (double)((n + 31) / 32);
-  const double Eb = 1.25 * ((L + 8.0) * 0x1p-24 * S1 + 0x1p-46 * sub.st->lam_absmax * S2) +
+  const double Eb = 1.25 * ((L + 16.0) * 0x1p-24 * S1 + 0x1p-46 * sub.st->lam_absmax * S2) +
                     64.0 * K * 0x1p-24 * sqrt((double)bsq);
   const bool okj = lane >= K || rng || fabs((double)v) > 2.0 * Eb;
   const bool ok = __all_sync(0xffffffffu, okj) && (Eb < INFINITY);
@@ -1037,7 +1047,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const int count = below + __popc(posmask) - posD - sub.kplus;
       // FP32 phase: the count is exact when no eigenvalue of Z can change sign
       // under the error of the FP32 sums, which only enters the K x K block:
-      //   E = |dM^|_2 <= (L + 8) 2^-24 S1 + 2^-46 max|lam| S2   (L terms per lane),
+      //   E = |dM^|_2 <= (L + 16) 2^-24 S1 + 2^-46 max|lam| S2   (L terms per lane,
+      //   three roundings per term, five in the warp's FP32 butterfly, slack),
       // plus the Jacobi's own rounding.  Eigenvalues with |z_j| > 2E keep their
       // sign (Weyl).  The small ones belong to eigenvectors that live almost
       // entirely in the two bordered rows; with s the small set, W = |V_{K,s}|_F^2
@@ -1053,7 +1064,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
         const double L = (double)((n + 31) / 32);
-        const double E = 1.25 * ((L + 8.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
+        const double E = 1.25 * ((L + 16.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
                          64.0 * kEps * zmax;
         const bool small = lane < Z2 && !(fabs(zj) > 2.0 * E);
         double wk = 0.0;
