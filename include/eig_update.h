@@ -150,14 +150,21 @@ int eig_update_rank_k(eig_handle h, eig_problem* prob, eig_report* rep, void* st
 
 /* ---- many updates ---------------------------------------------------------
  * Enqueue `count` independent updates (different n and k allowed) and return
- * one ticket per problem in tickets[] (host).  Problems whose n is at most
- * EIG_BATCH_SMALL_N are solved together in one persistent launch (one CTA
- * per problem); larger ones are solved one after another on the same stream.
- * Asynchronous: poll with eig_update_query(EIG_Q_STATUS).  The problem
- * arrays must stay valid until their tickets complete. */
-#define EIG_BATCH_SMALL_N 2048
+ * one ticket per problem in tickets[] (host).  The problems of one call form
+ * one table (two when some want eigenvectors and some do not), and every
+ * stage runs as one grouped launch over all of them.  Asynchronous: poll with
+ * eig_update_query(EIG_Q_STATUS / EIG_Q_REPORT).  The problem arrays must stay
+ * valid until their tickets complete.  A ticket holds host resources until
+ * eig_update_release (or eig_update_destroy); its id is never reused. */
 int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* tickets,
                      void* stream);
+
+/* Release a finished ticket of eig_update_batch: its status is folded into the
+ * EIG_Q_METRICS counters and the id becomes invalid (EIG_EINVAL from then on).
+ * The pinned status block and event of a batch call are freed with the last of
+ * its tickets.  Returns EIG_OK, EIG_EBUSY (still running: nothing released) or
+ * EIG_EINVAL (unknown or already released id). */
+int eig_update_release(eig_handle h, uint64_t ticket);
 
 /* ---- queries --------------------------------------------------------------
  * what = EIG_Q_STATUS:      in = const uint64_t* ticket, out = int32_t* status

@@ -20,7 +20,7 @@ __all__ = [
     "EIG_ENOTSUP", "EIG_EBUSY", "EIG_FP64", "EIG_MIXED", "EIG_VALUES", "EIG_VECTORS",
     "EIG_REPORT", "EIG_ASYNC", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT", "EIG_Q_LAST_STATUS",
     "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EIG_Q_METRICS", "EigError", "lib", "library_path", "colmajor",
-    "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
+    "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch", "eig_update_release",
     "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
         L.eig_update_destroy.argtypes = [vp]
         L.eig_update_rank_k.argtypes = [vp, ctypes.POINTER(eig_problem), ctypes.POINTER(eig_report), vp]
         L.eig_update_batch.argtypes = [vp, i32, ctypes.POINTER(eig_problem), ctypes.POINTER(ctypes.c_uint64), vp]
+        L.eig_update_release.argtypes = [vp, ctypes.c_uint64]
         L.eig_update_query.argtypes = [vp, i32, vp, vp, ctypes.c_size_t]
         L.eig_project.argtypes = [vp, i64, i32, vp, vp, vp, vp]
         L.eig_secular_values.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp]
@@ -145,7 +146,7 @@ def lib() -> ctypes.CDLL:
             getattr(L, f).restype = ctypes.c_int
         L.eig_version.restype = ctypes.c_char_p
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
-                  "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
+                  "eig_update_release", "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
                   "eig_secular_values_static", "eig_location_rank2", "eig_perturbation",
                   "eig_update_select"):
             getattr(L, f).restype = ctypes.c_int
@@ -256,11 +257,21 @@ def eig_update_batch(h, problems, stream=None):
         keep.append(sb)
     tickets = (ctypes.c_uint64 * max(1, len(problems)))()
     _check(lib().eig_update_batch(h, len(problems), arr, tickets, _stream(stream)), "eig_update_batch")
-    _batch_keepalive.append((arr, keep))
-    return [int(tickets[i]) for i in range(len(problems))]
+    ids = [int(tickets[i]) for i in range(len(problems))]
+    for t in ids:  # the call's host buffers live until its tickets are released
+        _batch_keepalive[(h.value if hasattr(h, "value") else h, t)] = (arr, keep)
+    return ids
 
 
-_batch_keepalive = []
+def eig_update_release(h, ticket: int) -> int:
+    """Free a finished batch ticket (EIG_EBUSY while it runs, EIG_EINVAL if unknown)."""
+    rc = lib().eig_update_release(h, int(ticket))
+    if rc == EIG_OK:
+        _batch_keepalive.pop((h.value if hasattr(h, "value") else h, int(ticket)), None)
+    return rc
+
+
+_batch_keepalive = {}
 
 
 def eig_update_query(h, what: int, ticket: int | None = None):

@@ -24,14 +24,24 @@ constexpr int kCheckCols = 16;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Completion resources of one eig_update_batch call, shared by its tickets
+// and freed when the last of them is released.
+struct BatchRes {
+  cudaEvent_t done = nullptr;  // recorded after the call's last launch
+  DevStatus* host = nullptr;   // pinned: one device status per problem of the call
+  int live = 0;                // tickets of the call not released yet
+};
+
+// One problem of a batch.  Its id is (gen << 32) | (index + 1): a released
+// slot is reused with gen + 1, so an id is never valid twice.
 struct Ticket {
-  cudaEvent_t done = nullptr;
-  DevStatus* host = nullptr;   // pinned copy of the device status at completion
-  double* chk_host = nullptr;  // pinned copy of the check results (may be null)
+  int batch = -1;               // index into eig_ctx::batches
+  int slot = 0;                 // status slot in the batch's pinned block
   int64_t n = 0;
   int32_t k = 0;
   int32_t pre_status = EIG_OK;  // host-side failure before launch
-  bool report = false;
+  uint32_t gen = 0;
+  bool live = false;
 };
 
 // Sub-buffers of one update, carved from the handle's workspace.
@@ -163,6 +173,9 @@ struct eig_ctx {
   int64_t m_unread = 0;  // EIG_ASYNC updates superseded before their status was read
   std::mutex mu;
   std::vector<Ticket> tickets;
+  std::vector<int> free_tickets;
+  std::vector<BatchRes> batches;
+  std::vector<int> free_batches;
 };
 
 namespace {
@@ -614,10 +627,9 @@ int eig_update_destroy(eig_handle h) {
   {
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
-    for (Ticket& t : h->tickets) {
-      if (t.done) cudaEventDestroy(t.done);
-      if (t.host) cudaFreeHost(t.host);
-      if (t.chk_host) cudaFreeHost(t.chk_host);
+    for (BatchRes& b : h->batches) {
+      if (b.done) cudaEventDestroy(b.done);
+      if (b.host) cudaFreeHost(b.host);
     }
     if (h->ws) cudaFree(h->ws);
     if (h->st_host) cudaFreeHost(h->st_host);
@@ -760,42 +772,123 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
   }
   int rc = ensure_ws(h, need);
   if (rc) return rc;
-  std::vector<Ticket> made(count);
-  for (int i = 0; i < count; ++i) {
-    Ticket& t = made[i];
-    t.n = probs[i].n;
-    t.k = probs[i].k;
-    t.pre_status = pre[i];
-    if (cudaMallocHost(&t.host, sizeof(DevStatus)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      return EIG_ENOMEM;
-    }
-    std::memset(t.host, 0, sizeof(DevStatus));
+  // One pinned status block and one event for the whole call.
+  BatchRes B;
+  if (cudaMallocHost(&B.host, sizeof(DevStatus) * (size_t)count) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (B.host) cudaFreeHost(B.host);
+    return EIG_ENOMEM;
   }
+  std::memset(B.host, 0, sizeof(DevStatus) * (size_t)count);
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(s);  // copies into B.host may be queued
+    cudaGetLastError();
+    cudaEventDestroy(B.done);
+    cudaFreeHost(B.host);
+    return code;
+  };
   for (int v = 0; v < 2; ++v) {
     if (tab[v].empty()) continue;
     std::vector<char> img;
     Table T = layout_table(h, tab[v], h->ws, v == 1, mixed, &img);
-    if (T.bytes == 0) return EIG_ECUDA;
+    if (T.bytes == 0) return fail(EIG_ECUDA);
     int nl = 0;
     rc = enqueue_table(h, T, (int)tab[v].size(), v == 1, mixed, false, s, nullptr, &nl, img, nullptr, 0);
-    if (rc) return rc;
+    if (rc) return fail(rc);
     {
       std::lock_guard<std::mutex> lk(h->mu);
       h->m_launches += nl;
     }
     for (size_t j = 0; j < tab[v].size(); ++j)
-      CK(cudaMemcpyAsync(made[slot[v][j]].host, T.d_st + j, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      if (cudaMemcpyAsync(B.host + slot[v][j], T.d_st + j, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess)
+        return fail(EIG_ECUDA);
     // The next table reuses the workspace: keep the tables stream-ordered.
   }
+  if (cudaEventRecord(B.done, s) != cudaSuccess) return fail(EIG_ECUDA);
   std::lock_guard<std::mutex> lk(h->mu);
+  int bi;
+  if (!h->free_batches.empty()) {
+    bi = h->free_batches.back();
+    h->free_batches.pop_back();
+  } else {
+    bi = (int)h->batches.size();
+    h->batches.emplace_back();
+  }
+  B.live = count;
+  h->batches[bi] = B;
   for (int i = 0; i < count; ++i) {
-    CK(cudaEventRecord(made[i].done, s));
-    h->tickets.push_back(made[i]);
-    tickets[i] = (uint64_t)h->tickets.size();  // 1-based
+    int ti;
+    if (!h->free_tickets.empty()) {
+      ti = h->free_tickets.back();
+      h->free_tickets.pop_back();
+    } else {
+      ti = (int)h->tickets.size();
+      h->tickets.emplace_back();
+    }
+    Ticket& t = h->tickets[ti];
+    t.batch = bi;
+    t.slot = i;
+    t.n = probs[i].n;
+    t.k = probs[i].k;
+    t.pre_status = pre[i];
+    t.live = true;
+    tickets[i] = ((uint64_t)t.gen << 32) | (uint64_t)(ti + 1);
+    ++h->m_updates;
+    h->m_pairs += probs[i].n > 0 ? probs[i].n : 0;
   }
   h->last_stream = s;
+  return EIG_OK;
+}
+
+// The live ticket an id names, or null (call with h->mu held).
+static Ticket* find_ticket(eig_ctx* h, uint64_t id) {
+  const uint64_t idx = (id & 0xffffffffull);
+  if (idx < 1 || idx > h->tickets.size()) return nullptr;
+  Ticket& t = h->tickets[idx - 1];
+  if (!t.live || t.gen != (uint32_t)(id >> 32)) return nullptr;
+  return &t;
+}
+
+// Final status of a ticket (EIG_EBUSY while its batch runs).  Call with h->mu held.
+static int ticket_status(eig_ctx* h, const Ticket& t, DevStatus* st_out) {
+  if (t.pre_status != EIG_OK) return t.pre_status;
+  const BatchRes& b = h->batches[t.batch];
+  const cudaError_t q = cudaEventQuery(b.done);
+  if (q == cudaErrorNotReady) {
+    cudaGetLastError();
+    return EIG_EBUSY;
+  }
+  if (q != cudaSuccess) {
+    cudaGetLastError();
+    return EIG_ECUDA;
+  }
+  if (st_out) *st_out = b.host[t.slot];
+  return status_of(b.host[t.slot]);
+}
+
+int eig_update_release(eig_handle h, uint64_t ticket) {
+  if (!h) return EIG_EINVAL;
+  DeviceGuard g(h->device);
+  if (!g.ok) return EIG_ECUDA;
+  std::lock_guard<std::mutex> lk(h->mu);
+  Ticket* t = find_ticket(h, ticket);
+  if (!t) return EIG_EINVAL;
+  const int status = ticket_status(h, *t, nullptr);
+  if (status == EIG_EBUSY) return EIG_EBUSY;
+  if (status == EIG_OK) ++h->m_ok;
+  else ++h->m_failed;
+  t->live = false;
+  ++t->gen;
+  h->free_tickets.push_back((int)((ticket & 0xffffffffull) - 1));
+  BatchRes& b = h->batches[t->batch];
+  if (--b.live == 0) {
+    cudaEventDestroy(b.done);
+    cudaFreeHost(b.host);
+    b = BatchRes{};
+    h->free_batches.push_back(t->batch);
+  }
   return EIG_OK;
 }
 
@@ -809,23 +902,14 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       if (!in) return EIG_EINVAL;
       const uint64_t id = *static_cast<const uint64_t*>(in);
       Ticket t;
+      DevStatus dst{};
+      int status;
       {
         std::lock_guard<std::mutex> lk(h->mu);
-        if (id < 1 || id > h->tickets.size()) return EIG_EINVAL;
-        t = h->tickets[id - 1];
-      }
-      int status = t.pre_status;
-      if (status == EIG_OK) {
-        const cudaError_t q = cudaEventQuery(t.done);
-        if (q == cudaErrorNotReady) {
-          cudaGetLastError();
-          status = EIG_EBUSY;
-        } else if (q != cudaSuccess) {
-          cudaGetLastError();
-          status = EIG_ECUDA;
-        } else {
-          status = status_of(*t.host);
-        }
+        const Ticket* tp = find_ticket(h, id);
+        if (!tp) return EIG_EINVAL;
+        t = *tp;
+        status = ticket_status(h, t, &dst);
       }
       if (what == EIG_Q_STATUS) {
         if (!out || out_bytes < sizeof(int32_t)) return EIG_EINVAL;
@@ -837,7 +921,7 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       eig_problem P{};
       P.n = t.n;
       P.k = t.k;
-      fill_report(static_cast<eig_report*>(out), &P, *t.host, t.report ? t.chk_host : nullptr, status);
+      fill_report(static_cast<eig_report*>(out), &P, dst, nullptr, status);
       return status;
     }
     case EIG_Q_LAST_STATUS: {
@@ -869,25 +953,11 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       m.launches = h->m_launches;
       m.workspace_allocs = h->m_allocs;
       m.workspace_bytes = h->ws_bytes;
-      for (const Ticket& t : h->tickets) {  // batch problems: resolved now, without waiting
-        ++m.updates;
-        m.eigenpairs += t.n > 0 ? t.n : 0;
-        int status = t.pre_status;
-        if (status == EIG_OK) {
-          const cudaError_t q = cudaEventQuery(t.done);
-          if (q == cudaErrorNotReady) {
-            cudaGetLastError();
-            ++m.updates_pending;
-            continue;
-          }
-          if (q != cudaSuccess) {
-            cudaGetLastError();
-            status = EIG_ECUDA;
-          } else {
-            status = status_of(*t.host);
-          }
-        }
-        if (status == EIG_OK) ++m.updates_ok;
+      for (const Ticket& t : h->tickets) {  // live batch tickets: resolved now, without waiting
+        if (!t.live) continue;
+        const int status = ticket_status(h, t, nullptr);
+        if (status == EIG_EBUSY) ++m.updates_pending;
+        else if (status == EIG_OK) ++m.updates_ok;
         else ++m.updates_failed;
       }
       m.updates_pending += h->m_unread + (h->last_counted ? 0 : 1);

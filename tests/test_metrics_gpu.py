@@ -70,3 +70,45 @@ def test_metrics_count_every_kind_of_update(eu):
         assert np.all(np.diff([m0["launches"], m1["launches"], m3["launches"], m5["launches"]]) >= 0)
     finally:
         eu.eig_update_destroy(h)
+
+
+def test_batch_tickets_are_released_and_never_reused(eu):
+    """eig_update_release frees a finished ticket; its id stays invalid even
+    when the slot is reused by a later batch; the counters keep its outcome."""
+    import torch
+
+    h = eu.eig_update_init(0, eu.EIG_FP64)
+    try:
+        Ps = [workloads.general(n, 2, seed=n, sigma="psd") for n in (50, 90, 130)]
+        ds = [_dev(p) for p in Ps]
+        ds[2]["lam"] = dev_vec(Ps[2]["lam"][::-1].copy())  # fails on the device
+        first = eu.eig_update_batch(h, ds)
+        rel = [eu.eig_update_release(h, t) for t in first]  # possibly still running
+        assert all(r in (0, eu.EIG_EBUSY) for r in rel)
+        torch.cuda.synchronize()
+        for t, r in zip(first, rel):
+            if r == eu.EIG_EBUSY:
+                assert eu.eig_update_release(h, t) == 0
+        for t in first:
+            assert eu.eig_update_query(h, eu.EIG_Q_STATUS, t) == eu.EIG_EINVAL
+            assert eu.eig_update_release(h, t) == eu.EIG_EINVAL  # twice: unknown
+        m = eu.eig_update_query(h, eu.EIG_Q_METRICS)
+        assert (m["updates"], m["updates_ok"], m["updates_failed"], m["updates_pending"]) == (3, 2, 1, 0)
+
+        ds2 = [_dev(p) for p in Ps[:2]]
+        second = eu.eig_update_batch(h, ds2)
+        torch.cuda.synchronize()
+        assert not set(second) & set(first)  # reused slots carry a new generation
+        assert [eu.eig_update_query(h, eu.EIG_Q_STATUS, t) for t in second] == [0, 0]
+        for t in first:
+            assert eu.eig_update_query(h, eu.EIG_Q_STATUS, t) == eu.EIG_EINVAL
+        rc, rep = eu.eig_update_query(h, eu.EIG_Q_REPORT, second[1])
+        assert rc == 0 and rep["n"] == 90
+        assert all(eu.eig_update_release(h, t) == 0 for t in second)
+        m = eu.eig_update_query(h, eu.EIG_Q_METRICS)
+        assert (m["updates"], m["updates_ok"], m["updates_failed"], m["updates_pending"]) == (5, 4, 1, 0)
+        # releasing touches no result: the caller's buffers hold the updates
+        lam_new = ds2[0]["lam"].cpu().numpy()
+        assert np.all(np.diff(lam_new) >= 0) and not np.array_equal(lam_new, Ps[0]["lam"])
+    finally:
+        eu.eig_update_destroy(h)
