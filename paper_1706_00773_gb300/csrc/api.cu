@@ -481,8 +481,8 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   MARK(2);
   for (size_t c = 0; c < T.classes.size(); ++c) {
     CK(launch_class_prefix(T.d_desc, T.classes[c], s));
-    CK(launch_counts_grouped(T.d_desc, T.classes[c], T.class_items[c], s));
-    nl += 2;
+    CK(launch_counts_grouped(T.d_desc, T.classes[c], T.class_items[c], mixed, s));
+    nl += mixed ? 3 : 2;
   }
   MARK(3);
   for (size_t c = 0; c < T.classes.size(); ++c) {

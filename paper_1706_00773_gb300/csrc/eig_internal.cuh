@@ -253,7 +253,8 @@ cudaError_t launch_runs_rotate_q_grouped(const ProbDesc* P, int count, int num_s
 // Prefix sums of n_keep and n_defl over a class (one small kernel).
 cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStream_t s);
 // Grouped secular stages for one class (pole counts, zero finder, assembly).
-cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s);
+cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, bool mixed,
+                                  cudaStream_t s);
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
                                  int num_sms, cudaStream_t s);
 // Order the zero finder's work: roots in pole intervals that hold several roots

@@ -657,7 +657,11 @@ __device__ void count_tail_f32(const Sub& sub, int n, int pole, const double* M,
   __syncwarp();
 }
 
-template <int K>
+// CM selects the passes: 0 = FP32 then, if uncertified, FP64 (one kernel);
+// 1 = the FP32 pass only, an uncertified count written as -1; 2 = the FP64
+// pass only (the recount launch after a CM = 1 launch).  Split in two launches
+// the FP32 pass needs half the registers, so twice the warps stay resident.
+template <int K, int CM = 0>
 __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, bool absolute,
                                             double tau, double lam_o, int pole, int* out, double* M0,
                                             double* Gm, double* Vg, double* Ev, double* s_err, int* s_redo,
@@ -669,9 +673,10 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
   // that the error bound cannot certify is taken again in FP64.  A repeated
   // or nearly repeated pole gives 1/0 in FP32, an infinite bound, and so the
   // FP64 pass.
-  const bool try32 = !absolute && sub.lamf != nullptr;
-  for (int pass = try32 ? 0 : 1; pass < 2; ++pass) {
-    const bool p32 = (pass == 0);
+  const bool try32 = !absolute && sub.lamf != nullptr && CM != 2;
+  constexpr int kLast = (CM == 1) ? 0 : 1;  // CM = 1 never compiles the FP64 pass
+  for (int pass = try32 ? 0 : 1; pass <= kLast; ++pass) {
+    const bool p32 = (CM == 1) ? true : (CM == 2) ? false : (pass == 0);
     double* M = M0;
     int below = 0;
     if (active) {
@@ -758,6 +763,8 @@ __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, 
     group_sync<E>(g);
     if (!p32 || !active || (*s_redo) == 0) break;
   }
+  if (CM == 1 && active && e == 0 && lane == 0 && (!try32 || (*s_redo) != 0)) *out = -1;  // recount in FP64
+  __syncwarp();
 }
 
 template <int K>
@@ -790,7 +797,7 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
 }
 
 // Pole counts of every update of a class (items numbered across the class).
-template <int K>
+template <int K, int CM>
 __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __restrict__ P,
                                                              ClassDesc c) {
   constexpr int E = warps_per_root(K);
@@ -820,10 +827,11 @@ __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __r
         pt = item - c.pk[p];
         lam_o = sub.lam[pt];
         out = d.pole_cnt + pt;
+        if (CM == 2 && *out >= 0) active = false;  // certified by the FP32 launch
       }
     }
-    count_point<K>(sub, n, active, false, 0.0, lam_o, pt, out, sM[g], sG[g], sV[g], sEv[g], s_err[g], &s_redo[g],
-                   g, e, lane);
+    count_point<K, CM>(sub, n, active, false, 0.0, lam_o, pt, out, sM[g], sG[g], sV[g], sEv[g], s_err[g],
+                       &s_redo[g], g, e, lane);
   }
 }
 
@@ -1887,12 +1895,19 @@ namespace {
 int g_occ_roots_grouped[17];
 
 template <int K>
-cudaError_t counts_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s) {
+cudaError_t counts_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, bool mixed, cudaStream_t s) {
   constexpr int G = 4 / warps_per_root(K);
   int blocks = (max_items + G - 1) / G;
   if (blocks < 1) blocks = 1;
   if (blocks > 65535) blocks = 65535;
-  counts_grouped_kernel<K><<<blocks, 128, 0, s>>>(P, c);
+  if (!mixed) {
+    counts_grouped_kernel<K, 0><<<blocks, 128, 0, s>>>(P, c);
+    return cudaGetLastError();
+  }
+  counts_grouped_kernel<K, 1><<<blocks, 128, 0, s>>>(P, c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  counts_grouped_kernel<K, 2><<<blocks, 128, 0, s>>>(P, c);
   return cudaGetLastError();
 }
 
@@ -1934,9 +1949,10 @@ cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s) {
+cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, bool mixed,
+                                  cudaStream_t s) {
   switch (c.K) {
-#define C_(K_) case K_: return counts_grouped_k<K_>(P, c, max_items, s);
+#define C_(K_) case K_: return counts_grouped_k<K_>(P, c, max_items, mixed, s);
     C_(1) C_(2) C_(3) C_(4) C_(5) C_(6) C_(7) C_(8) C_(10) C_(12) C_(14) C_(16)
 #undef C_
     default: return cudaErrorInvalidValue;
