@@ -661,12 +661,12 @@ __device__ void count_tail_f32(const Sub& sub, int n, int pole, const double* M,
 // 1 = the FP32 pass only, an uncertified count written as -1; 2 = the FP64
 // pass only (the recount launch after a CM = 1 launch).  Split in two launches
 // the FP32 pass needs half the registers, so twice the warps stay resident.
-template <int K, int CM = 0>
+template <int K, int CM = 0, int EP = 0>
 __device__ __forceinline__ void count_point(const Sub& sub, int n, bool active, bool absolute,
                                             double tau, double lam_o, int pole, int* out, double* M0,
                                             double* Gm, double* Vg, double* Ev, double* s_err, int* s_redo,
                                             int g, int e, int lane) {
-  constexpr int E = warps_per_root(K);
+  constexpr int E = EP ? EP : warps_per_root(K);  // warps per point
   constexpr int KP = K + 1;
   // At a pole with FP32 copies present, a first pass sums M~ in FP32 and does
   // the k x k work in FP32 too (count_tail_f32, #{lam_i < lam_q} = q); a count
@@ -797,10 +797,14 @@ __global__ void __launch_bounds__(128) counts_kernel(Sub sub, const double* __re
 }
 
 // Pole counts of every update of a class (items numbered across the class).
+// The recount (CM = 2) gives each point up to four warps, each owning a share
+// of the k x k accumulators: a recount is one FP64 pass over all n' terms, and
+// the launch lasts as long as its slowest recount.
 template <int K, int CM>
 __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __restrict__ P,
                                                              ClassDesc c) {
-  constexpr int E = warps_per_root(K);
+  // (warp e owns rows e and K-1-e, so E <= ceil(K/2))
+  constexpr int E = (CM == 2) ? (K >= 7 ? 4 : K >= 3 ? 2 : 1) : warps_per_root(K);
   constexpr int G = 4 / E;
   constexpr int KP = K + 1;
   __shared__ double sM[G][K * KP], sG[G][K * KP], sV[G][K * KP];
@@ -830,8 +834,8 @@ __global__ void __launch_bounds__(128) counts_grouped_kernel(const ProbDesc* __r
         if (CM == 2 && *out >= 0) active = false;  // certified by the FP32 launch
       }
     }
-    count_point<K, CM>(sub, n, active, false, 0.0, lam_o, pt, out, sM[g], sG[g], sV[g], sEv[g], s_err[g],
-                       &s_redo[g], g, e, lane);
+    count_point<K, CM, E>(sub, n, active, false, 0.0, lam_o, pt, out, sM[g], sG[g], sV[g], sEv[g], s_err[g],
+                          &s_redo[g], g, e, lane);
   }
 }
 
@@ -1907,7 +1911,11 @@ cudaError_t counts_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_item
   counts_grouped_kernel<K, 1><<<blocks, 128, 0, s>>>(P, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  counts_grouped_kernel<K, 2><<<blocks, 128, 0, s>>>(P, c);
+  constexpr int G2 = (K >= 7) ? 1 : (K >= 3 ? 2 : 4);  // points per CTA of the recount
+  int blocks2 = (max_items + G2 - 1) / G2;
+  if (blocks2 < 1) blocks2 = 1;
+  if (blocks2 > 65535) blocks2 = 65535;
+  counts_grouped_kernel<K, 2><<<blocks2, 128, 0, s>>>(P, c);
   return cudaGetLastError();
 }
 
