@@ -230,7 +230,8 @@ int eig_project(eig_handle h, int64_t n, int32_t k, const double* Q, const doubl
 
 /* Eigenvalues of diag(lambda) + U Sigma U^T (Sec. 2.2-2.3) without vectors:
    mu (device n, ascending) receives them; iters (device int32 n, may be NULL)
-   the evaluations each root took (0 for deflated pairs).  Synchronous. */
+   the evaluations each root took (0 for deflated pairs).  U is read only: runs
+   of exactly equal lambda are rotated in a workspace copy.  Synchronous. */
 int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
                        const int8_t* sigma, double* mu, int32_t* iters, void* stream);
 
