@@ -60,7 +60,22 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving measurement")
     ap.add_argument("--no-comparisons", action="store_true",
                     help="skip the interval query, eq. (11) and rank-1 chain comparisons")
+    ap.add_argument("--k-sweep", default="4,16",
+                    help="other ranks of the n=8192 workload timed beside the headline (comma list, '' = none)")
     return ap.parse_args()
+
+
+def rnd(v, digits: int = 4):
+    """Round floats (recursively) to `digits` significant digits for the JSON line."""
+    if isinstance(v, float):
+        if v != v or v in (float("inf"), float("-inf")) or v == 0.0:
+            return v
+        return float("%.*g" % (digits, v))
+    if isinstance(v, dict):
+        return {k: rnd(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [rnd(x, digits) for x in v]
+    return v
 
 
 # ---------------------------------------------------------------------------
@@ -667,6 +682,24 @@ def main():
         fp64 = {"value": R64["value"], "unit": UNIT, "ms_per_step": R64["ms"] / len(R64["reps"]),
                 "latency_ms": {"p50": R64["p50"], "p99": R64["p99"]}}
 
+    # ---- the same workload at the other ranks of the general rank-k config
+    k_sweep = {}
+    for kk in [int(x) for x in args.k_sweep.split(",") if x.strip()]:
+        if kk == k:
+            continue
+        Pk = workloads.general_rank_k(k=kk, seed=2000 + rank, n=n, device=None if args.host_inputs else dev)
+        hk = eu.eig_update_init(local, main_mode)
+        Rk = run_mode(eu, hk, Pk, dev, max(1, min(args.steps, 5)), 2, world)
+        eu.eig_update_destroy(hk)
+        rk = Rk["reps"]
+        k_sweep[str(kk)] = {"value": Rk["value"], "ms_per_step": Rk["ms"] / len(rk),
+                            "p99_ms": Rk["p99"], "roots_ms": statistics.fmean(r["ms_roots"] for r in rk),
+                            "gemm_ms": statistics.fmean(r["ms_gemm"] for r in rk),
+                            "counts_ms": statistics.fmean(r["ms_counts"] for r in rk),
+                            "evals_per_root": statistics.fmean(r["iters_total"] for r in rk) / n,
+                            "notconv": int(sum(r["n_notconv"] for r in rk))}
+        del Pk
+
     comparisons = None
     if not args.no_comparisons and world == 1:
         comparisons = run_comparisons(eu, dev, main_mode, P, R["ms"] / args.steps)
@@ -677,6 +710,17 @@ def main():
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(eu, dev, main_mode)
+
+    # ---- the FP64 pipe's measured FMA rate (denominator beside the derived peak)
+    fp64_meas = None
+    try:
+        clk2 = ClockSampler(local)
+        clk2.start()
+        fp64_meas = eu.eig_fp64_fma_rate(local, 20)
+        time.sleep(0.3)
+        fp64_clk = clk2.stop()
+    except Exception as exc:  # measurement only: the line records why it is missing
+        fp64_clk = {"error": type(exc).__name__}
 
     # ---- rooflines from the library's own per-stage CUDA events
     peaks, psrc = measured_peaks()
@@ -691,17 +735,18 @@ def main():
     f64, f32 = secular_flops(n_keep, k, evals, evals32, mixed)
     roots_s = stage["ms_roots"] / 1000.0
     roots_ach = f64 / roots_s / 1e9
-    roof_roots = {"kernel": "roots_grouped_kernel<8>", "bound": "alu", "achieved": roots_ach,
+    roof_roots = {"kernel": "roots_grouped_kernel<%d>" % k, "bound": "alu", "achieved": roots_ach,
                   "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": roots_ach / FP64_PEAK_GFLOPS,
                   "traffic": load_traffic("roots_grouped_kernel"),
-                  "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
-                  "work": ("%.0f FP64 evaluations x n'(k(k+1)+2) FP64 flops per launch (M, shift, reciprocal)"
-                           % evals) if mixed else ("%.0f evaluations x n'(2k(k+1)+2) FP64 flops per launch" % evals),
-                  "fp32": ({"achieved": f32 / roots_s / 1e9, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
-                            "frac": f32 / roots_s / 1e9 / FP32_PEAK_GFLOPS,
-                            "work": "%.0f FP32 evaluations x n'(2k(k+1)+2) + N of the FP64 ones, n' k(k+1)" % evals32}
-                           if mixed else None),
-                  "first_order_updates": taylor}
+                  "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe nominal)",
+                  "peak_measured": fp64_meas,
+                  "frac_of_measured": (roots_ach / fp64_meas) if fp64_meas else None,
+                  "work": ("%.0f FP64 evaluations x n'(k(k+1)+2) FP64 flops (M, shift, reciprocal)"
+                           % evals) if mixed else ("%.0f evaluations x n'(2k(k+1)+2) FP64 flops" % evals)}
+    roots_fp32 = ({"achieved": f32 / roots_s / 1e9, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
+                   "frac": f32 / roots_s / 1e9 / FP32_PEAK_GFLOPS,
+                   "work": "%.0f FP32 evaluations x n'(2k(k+1)+2) + N of the FP64 ones, n' k(k+1)" % evals32}
+                  if mixed else None)
     if main_mode == eu.EIG_MIXED:
         gflops = 15 * 2.0 * n ** 3
         peak_t = float(peaks.get("bf16_tflops_sustained", 1700.0)) * 1000.0
@@ -717,12 +762,24 @@ def main():
         roof_gemm = {"kernel": "gemm_f64_grouped_kernel", "bound": "alu", "achieved": g_ach, "peak": FP64_PEAK_GFLOPS,
                      "unit": "GFLOP/s", "frac": g_ach / FP64_PEAK_GFLOPS,
                      "traffic": load_traffic("gemm_f64_grouped_kernel"),
-                     "peak_source": "FP64 pipe (recipe nominal)", "work": "2 n^3 flops"}
+                     "peak_source": "FP64 pipe (recipe nominal)", "peak_measured": fp64_meas,
+                     "frac_of_measured": (g_ach / fp64_meas) if fp64_meas else None, "work": "2 n^3 flops"}
     dominant = roof_roots if stage["ms_roots"] >= stage["ms_gemm"] else roof_gemm
     other = roof_gemm if dominant is roof_roots else roof_roots
+    dtype = ("f64 secular finish + certified f32 coarse/pole counts + split-bf16x5 (X=QW, tcgen05)"
+             if mixed else "f64")
+    # The detail line (printed first): everything too long for the headline line.
+    detail = {"bench_detail": {
+        "comparisons": comparisons, "roofline_other": other, "roots_fp32": roots_fp32,
+        "batched": batched, "serving": serving, "k_sweep": k_sweep,
+        "fp64_fma_rate": {"gflops": fp64_meas, "clocks": fp64_clk},
+        "e2e_how": e2e_note, "serial_update_with_copies_ms": e2e_serial_ms,
+        "evals_per_root": evals / max(1, n_keep), "fp32_evals_per_root": evals32 / max(1, n_keep),
+        "first_order_updates_per_root": taylor / max(1, n_keep)}}
+    summ = lambda d, keys: ({kk: d.get(kk) for kk in keys} if d else None)
     line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": R["ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "k": k, "mode": args.mode,
                        "l2": "inputs larger than L2 (Q, X 537 MB; W slices 671 MB)",
                        "parallelism": "independent update per GPU"},
@@ -730,16 +787,22 @@ def main():
             "fp64_path": fp64,
             "speedup_vs_fp64_path": (R["value"] / fp64["value"]) if fp64 else None,
             "stages_ms": stage, "evals_per_root": evals / max(1, n_keep),
-            "fp32_evals_per_root": evals32 / max(1, n_keep), "first_order_updates_per_root": taylor / max(1, n_keep),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "how": e2e_note, "serial_update_with_copies_ms": e2e_serial_ms},
+            "k_sweep": {kk: summ(v, ("value", "ms_per_step", "roots_ms", "notconv")) for kk, v in k_sweep.items()},
+            "batched": summ(batched, ("value", "ms_per_step", "updates_per_step", "failed_updates",
+                                      "max_err_vs_oracle", "tuned_vs_untuned")),
+            "serving": summ(serving, ("value", "latency_ms", "residents", "requests", "drift_vs_oracle")),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
-            "batched": batched,
-            "serving": serving,
-            "comparisons": comparisons,
-            "roofline": dominant, "roofline_other": other, "clocks": clk}
+            "roofline": {kk: v for kk, v in dominant.items() if kk not in ("peak_source", "work")},
+            "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(P, args.cpu_sample)
+        cb = cpu_baseline(P, args.cpu_sample)
+        detail["bench_detail"]["cpu_baseline_sample"] = cb["sample"]
+        cb["sample"] = cb["sample"].split(";")[0]
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(rnd(detail)), flush=True)
+        line = rnd(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -174,8 +174,10 @@ int eig_update_release(eig_handle h, uint64_t ticket);
  * what = EIG_Q_LAST_STATUS: in = NULL, out = int32_t* (synchronises the handle's
  *                           last stream first)
  * what = EIG_Q_COUNT:       in = const eig_count_args*, out = NULL.  Root count
- *                           #{mu < x_j} of diag(lambda) + U Sigma U^T at host or
- *                           device points (the location sub-problem, Sec. 2.2);
+ *                           #{mu < x_j} of diag(lambda) + U Sigma U^T at device
+ *                           points (the location sub-problem, Sec. 2.2), taken
+ *                           in FP64 in both modes (the mixed path's certified
+ *                           FP32 counts run at poles: eig_pole_counts);
  *                           synchronous.
  * what = EIG_Q_WORKSPACE:   in = const eig_problem*, out = uint64_t* bytes the
  *                           handle needs for that problem.
@@ -234,6 +236,26 @@ int eig_project(eig_handle h, int64_t n, int32_t k, const double* Q, const doubl
    of exactly equal lambda are rotated in a workspace copy.  Synchronous. */
 int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
                        const int8_t* sigma, double* mu, int32_t* iters, void* stream);
+
+/* Root counts at the poles (Sec. 2.2, location sub-problem), exactly as the
+   update computes them in the handle's mode.  Input as eig_secular_values
+   (device lambda ascending, device U n x k column-major, host sigma).  Runs of
+   equal lambda are rotated in a workspace copy of U and small rows deflated
+   (the update's own rule); the n' kept poles lambda'_0 < ... < lambda'_{n'-1}
+   form the sub-problem, and for every kept pole q:
+     counts[q]   = #{mu' < lambda'_q} of diag(lambda') + U' Sigma U'^T (the
+                   limit from the left), the count the zero finder uses;
+     counts32[q] = EIG_MIXED: the certified FP32 pass's count, or -1 where its
+                   error bound could not certify it and the FP64 recount
+                   decided; EIG_FP64: -1 (there is no FP32 pass);
+     idx_keep[q] = the row of lambda / U that kept pole q came from.
+   counts, counts32 and idx_keep are device int32 arrays of n entries (the last
+   two may be NULL); entries q >= n' are left unspecified.  *n_keep (host)
+   receives n'.  Synchronous.  EIG_EINVAL for bad arguments or unsorted /
+   non-finite input (*n_keep = 0, outputs unspecified). */
+int eig_pole_counts(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
+                    const int8_t* sigma, int32_t* counts, int32_t* counts32, int32_t* idx_keep,
+                    int64_t* n_keep, void* stream);
 
 /* ---- eigenvalues without any device allocation ---------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
@@ -365,6 +387,17 @@ int eig_perturbation(eig_handle h, int64_t n, int32_t k, const double* Q, const 
 int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
                       const double* K, const int8_t* sigma, double vl, double vu, int64_t max_m,
                       double* mu, double* X, int64_t* m_out, void* stream);
+
+/* ---- measurement -----------------------------------------------------------
+ * FP64 FMA throughput of `device`, the denominator of the FP64-pipe rooflines
+ * (the zero finder, pole counts, assembly and the FP64 GEMM are bound by that
+ * pipe).  The paper has no counterpart: it is a measurement of the machine.
+ * Runs a kernel of independent FMA chains (no memory traffic) on every SM,
+ * `reps` timed launches (CUDA events on `stream`) after one warm-up, and
+ * writes the best rate to *gflops as 2 x FMAs / s / 1e9.  About 10-20 ms per
+ * launch.  Synchronous.  EIG_EINVAL for reps < 1 or a NULL output, EIG_ECUDA
+ * if the device cannot be used. */
+int eig_fp64_fma_rate(int32_t device, int32_t reps, double* gflops, void* stream);
 
 /* Library version string (static storage). */
 const char* eig_version(void);

@@ -25,7 +25,7 @@ __all__ = [
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
     "eig_server_poll", "eig_server_query", "eig_server_pending", "Server", "eig_location_rank2",
-    "eig_perturbation", "eig_update_select",
+    "eig_perturbation", "eig_update_select", "eig_pole_counts", "eig_fp64_fma_rate",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
@@ -134,6 +134,8 @@ def lib() -> ctypes.CDLL:
         L.eig_update_select.argtypes = [vp, i64, i32, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i64,
                                         vp, vp, ctypes.POINTER(i64), vp]
         L.eig_secular_values_static.argtypes = [i64, i32, vp, vp, vp, vp, vp, i32, vp]
+        L.eig_pole_counts.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64), vp]
+        L.eig_fp64_fma_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), vp]
         L.eig_server_create.argtypes = [ctypes.POINTER(eig_server_params), ctypes.POINTER(vp)]
         L.eig_server_destroy.argtypes = [vp]
         L.eig_server_add_resident.argtypes = [vp, i64, vp, vp, ctypes.POINTER(i32)]
@@ -148,7 +150,7 @@ def lib() -> ctypes.CDLL:
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
                   "eig_update_release", "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
                   "eig_secular_values_static", "eig_location_rank2", "eig_perturbation",
-                  "eig_update_select"):
+                  "eig_update_select", "eig_pole_counts", "eig_fp64_fma_rate"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -336,6 +338,34 @@ def eig_secular_values(h, lam, U, sigma, mu, iters=None, stream=None) -> int:
     return _check(rc, "eig_secular_values", ok=(EIG_OK, EIG_ENOTCONV))
 
 
+def _iptr(t, what: str):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32 or t.dim() != 1 or t.stride(0) != 1:
+        raise TypeError("%s must be a contiguous CUDA int32 vector" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def eig_pole_counts(h, lam, U, sigma, counts, counts32=None, idx_keep=None, stream=None):
+    """Pole counts of the deflated sub-problem as the update computes them in the
+    handle's mode (device int32 outputs of n entries).  Returns (status, n_keep)."""
+    n = int(lam.shape[0])
+    k = int(U.shape[1])
+    for t, nm in ((counts, "counts"), (counts32, "counts32"), (idx_keep, "idx_keep")):
+        if t is not None and int(t.numel()) < n:
+            raise ValueError("%s needs n entries" % nm)
+    sbuf, sp = _sigma_buf(sigma, k)
+    nk = ctypes.c_int64()
+    rc = lib().eig_pole_counts(h, n, k, _ptr(lam, "lambda"), _ptr(U, "U", True), sp, _iptr(counts, "counts"),
+                               _iptr(counts32, "counts32"), _iptr(idx_keep, "idx_keep"), ctypes.byref(nk),
+                               _stream(stream))
+    del sbuf
+    _check(rc, "eig_pole_counts")
+    return rc, int(nk.value)
+
+
 def eig_secular_values_static(lam, U, sigma, mu, iters=None, max_iter: int = 0, stream=None) -> int:
     """eig_secular_values without any device allocation (fixed library scratch,
     n <= EIG_STATIC_MAX_N); returns the status code without raising."""
@@ -347,6 +377,14 @@ def eig_secular_values_static(lam, U, sigma, mu, iters=None, max_iter: int = 0, 
                                          ip, max_iter, _stream(stream))
     del sbuf
     return rc
+
+
+def eig_fp64_fma_rate(device: int = 0, reps: int = 10, stream=None) -> float:
+    """Measured FP64 FMA throughput of the device, GFLOP/s (2 flops per FMA)."""
+    out = ctypes.c_double()
+    _check(lib().eig_fp64_fma_rate(int(device), int(reps), ctypes.byref(out), _stream(stream)),
+           "eig_fp64_fma_rate")
+    return float(out.value)
 
 
 def eig_make_rank2(n: int, j: int, a, K, stream=None):

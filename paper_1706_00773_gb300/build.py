@@ -1,6 +1,7 @@
 """Build libeigupdate.so in-tree for sm_103a with nvcc (no cmake).
 
-Each .cu under csrc/ is compiled in parallel to an object in _build/, then
+Each .cu under csrc/ is compiled in parallel to an object in _build/ (the
+per-rank secular kernels, secular_perk.cu, once per padded rank), then
 linked into paper_1706_00773_gb300/libeigupdate.so with the static CUDA
 runtime.  Objects are rebuilt when their source or any header is newer.
 """
@@ -18,6 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeigupdate.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+SECULAR_RANKS = (16, 8, 14, 12, 10, 7, 6, 5, 4, 3, 2, 1)  # largest first: they take longest
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "128",
          "-I", INCLUDE]
 
@@ -42,10 +44,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(OBJ, os.path.basename(s)[:-3] + ".o")
-        objs.append(o)
-        if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-c", s, "-o", o])
+        base = os.path.basename(s)[:-3]
+        # secular_perk.cu holds the secular kernels of one padded rank: one
+        # object per rank, compiled in parallel.
+        variants = [("_%d" % K, ["-DEIG_SECULAR_K=%d" % K]) for K in SECULAR_RANKS] if base == "secular_perk" \
+            else [("", [])]
+        for suffix, defs in variants:
+            o = os.path.join(OBJ, base + suffix + ".o")
+            objs.append(o)
+            if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
+                jobs.append([nvcc, *ARCH, *FLAGS, *defs, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

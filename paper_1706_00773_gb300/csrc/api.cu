@@ -1064,6 +1064,63 @@ int eig_secular_values(eig_handle h, int64_t n, int32_t k, const double* lambda,
   return status_of(*h->st_host);
 }
 
+int eig_pole_counts(eig_handle h, int64_t n, int32_t k, const double* lambda, const double* U,
+                    const int8_t* sigma, int32_t* counts, int32_t* counts32, int32_t* idx_keep, int64_t* n_keep,
+                    void* stream) {
+  if (!h || n < 1 || k < 1 || k > EIG_MAX_K || !lambda || !U || !counts || !n_keep ||
+      n > (int64_t)0x3fffffff)
+    return EIG_EINVAL;
+  unsigned long long negmask = 0;
+  int kplus = 0;
+  if (!sigma_info(sigma, k, &negmask, &kplus)) return EIG_EINVAL;
+  DeviceGuard g(h->device);
+  if (!g.ok) return EIG_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool mixed = h->mode == EIG_MIXED;
+  // The update's own launch sequence (a table of one, values only), stopped
+  // after the pole counts: the caller's U stands in for U = Q^T K.
+  eig_problem P{};
+  P.n = n;
+  P.k = k;
+  P.lambda = const_cast<double*>(lambda);
+  P.sigma = sigma;
+  std::vector<TableItem> items{{&P, negmask, kplus, false}};
+  const size_t need = layout_table(h, items, nullptr, false, mixed, nullptr).bytes;
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  std::vector<char> img;
+  Table T = layout_table(h, items, h->ws, false, mixed, &img);
+  if (T.bytes == 0 || T.classes.size() != 1) return EIG_ECUDA;
+  ProbDesc d0;
+  std::memcpy(&d0, img.data(), sizeof(ProbDesc));
+  CK(cudaMemcpyAsync(T.d_desc, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(T.d_st, 0, sizeof(DevStatus), s));
+  CK(cudaMemcpyAsync(d0.U, U, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+  CK(launch_runs_qr_grouped(T.d_desc, 1, n, s));
+  CK(launch_deflate_grouped(T.d_desc, 1, s));
+  CK(launch_class_prefix(T.d_desc, T.classes[0], s));
+  if (mixed) {
+    CK(launch_counts_grouped(T.d_desc, T.classes[0], T.class_items[0], true, s, 1));
+    if (counts32) CK(cudaMemcpyAsync(counts32, d0.pole_cnt, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_counts_grouped(T.d_desc, T.classes[0], T.class_items[0], true, s, 2));
+  } else {
+    CK(launch_counts_grouped(T.d_desc, T.classes[0], T.class_items[0], false, s));
+    if (counts32) CK(cudaMemsetAsync(counts32, 0xff, sizeof(int) * (size_t)n, s));
+  }
+  CK(cudaMemcpyAsync(h->st_host, T.d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int status = status_of(*h->st_host);
+  const int64_t nk = h->st_host->n_keep;
+  *n_keep = status == EIG_EINVAL ? 0 : nk;
+  if (status == EIG_EINVAL) return status;
+  if (nk > 0) {
+    CK(cudaMemcpyAsync(counts, d0.pole_cnt, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, s));
+    if (idx_keep) CK(cudaMemcpyAsync(idx_keep, d0.idx_keep, sizeof(int) * (size_t)nk, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return status;
+}
+
 int eig_perturbation(eig_handle h, int64_t n, int32_t k, const double* Q, const double* lambda,
                      const double* K, const int8_t* sigma, double* mu, double* X, void* stream) {
   if (!h || n < 1 || k < 1 || k > EIG_MAX_K || !Q || !lambda || !K || !mu || !X ||

@@ -253,8 +253,11 @@ cudaError_t launch_runs_rotate_q_grouped(const ProbDesc* P, int count, int num_s
 // Prefix sums of n_keep and n_defl over a class (one small kernel).
 cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStream_t s);
 // Grouped secular stages for one class (pole counts, zero finder, assembly).
+// Mixed-mode pole counts run as two launches: passes bit 1 = the certified
+// FP32 pass (an uncertified count is written as -1), bit 2 = the FP64 recount
+// of those; FP64 mode ignores passes.
 cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, bool mixed,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int passes = 3);
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
                                  int num_sms, cudaStream_t s);
 // Order the zero finder's work: roots in pole intervals that hold several roots
