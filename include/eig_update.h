@@ -90,6 +90,24 @@ typedef struct {
   double* Q_out;       /* device n x n output for the eigenvectors, or NULL */
   uint32_t want;       /* EIG_VALUES | EIG_VECTORS | EIG_REPORT | EIG_ASYNC */
   uint32_t pad2_;
+  double* errors;      /* device n x 4 (column-major, ld n) per-eigenpair error
+                          report, or NULL; filled when want has EIG_VECTORS.
+                          Row r belongs to the r-th new eigenpair (ascending):
+                            [r, 0] |(A' - mu_r) x_r|_2 / |A|, the residual of
+                                   the FP64 eq. (10) vector in the old
+                                   eigenbasis, (Lambda + U Sigma U^T - mu_r) w_r
+                                   with w_r unit (Sec. 3 metric (B) per pair;
+                                   deflated pairs: the bound |U|_F |u_i| / |A|);
+                            [r, 1] |rho_r - mu_r| / |A|, rho_r = w_r^T A' w_r
+                                   the Rayleigh quotient in FP64;
+                            [r, 2] min_{s != r} |mu_r - mu_s| / |A|;
+                            [r, 3] |w_r^T w_{r+1}| with the next secular root's
+                                   vector when that gap is below 1e-6 |A|
+                                   (Sec. 3 metric (C) where it is at risk), else 0.
+                          |A| = max|lambda_old| + |U|_F^2 (report.norm_A).  X = Q W
+                          adds the GEMM's own error on top (EIG_MIXED: the
+                          split-BF16 representation, <= 2^-41 per factor entry
+                          relative to its row / column maximum). */
 } eig_problem;
 
 typedef struct {
@@ -124,6 +142,9 @@ typedef struct {
   int64_t taylor_total;  /* evaluations taken by a first-order update of the
                             k x k sums after a tiny Newton step (no pass over
                             the terms) */
+  double max_pair_residual; /* with eig_problem.errors: max of its columns 0, */
+  double max_pair_rayleigh; /* 1 and 3 over every eigenpair (0 without) */
+  double max_pair_orth;
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

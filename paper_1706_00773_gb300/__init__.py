@@ -59,7 +59,7 @@ class eig_problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("Q", ctypes.c_void_p), ("lambda_", ctypes.c_void_p), ("K", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("Q_out", ctypes.c_void_p), ("want", ctypes.c_uint32),
-                ("pad2_", ctypes.c_uint32)]
+                ("pad2_", ctypes.c_uint32), ("errors", ctypes.c_void_p)]
 
 
 class eig_metrics(ctypes.Structure):
@@ -82,7 +82,9 @@ class eig_report(ctypes.Structure):
                 ("ms_counts", ctypes.c_double), ("ms_roots", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_slice", ctypes.c_double), ("ms_gemm", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("n_runs", ctypes.c_int32), ("iters32_total", ctypes.c_int64),
-                ("redo32_total", ctypes.c_int64), ("taylor_total", ctypes.c_int64)]
+                ("redo32_total", ctypes.c_int64), ("taylor_total", ctypes.c_int64),
+                ("max_pair_residual", ctypes.c_double), ("max_pair_rayleigh", ctypes.c_double),
+                ("max_pair_orth", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -227,19 +229,23 @@ def eig_update_destroy(h) -> None:
     _check(lib().eig_update_destroy(h), "eig_update_destroy")
 
 
-def _problem(Q, lam, K, sigma, want, Q_out=None):
+def _problem(Q, lam, K, sigma, want, Q_out=None, errors=None):
     n = int(lam.shape[0])
     k = int(K.shape[1]) if K.dim() == 2 else 1
     sbuf, sp = _sigma_buf(sigma, k)
+    if errors is not None and (tuple(errors.shape) != (n, 4) or errors.stride() != (1, n)):
+        raise ValueError("errors must be an n x 4 column-major float64 tensor (e.g. torch.empty(4, n).t())")
     P = eig_problem(n, k, 0, _ptr(Q, "Q", True), _ptr(lam, "lambda"), _ptr(K, "K", True), sp,
-                    _ptr(Q_out, "Q_out", True) if Q_out is not None else None, want, 0)
+                    _ptr(Q_out, "Q_out", True) if Q_out is not None else None, want, 0,
+                    _ptr(errors, "errors") if errors is not None else None)
     return P, sbuf
 
 
 def eig_update_rank_k(h, Q, lam, K, sigma=None, want: int = EIG_VALUES | EIG_VECTORS, Q_out=None,
-                      stream=None, raise_on_error: bool = True):
-    """One update in place (lam, and Q unless Q_out).  Returns (status, report dict)."""
-    P, keep = _problem(Q, lam, K, sigma, want, Q_out)
+                      stream=None, raise_on_error: bool = True, errors=None):
+    """One update in place (lam, and Q unless Q_out); errors: optional n x 4
+    column-major per-eigenpair report.  Returns (status, report dict)."""
+    P, keep = _problem(Q, lam, K, sigma, want, Q_out, errors)
     rep = eig_report()
     rc = lib().eig_update_rank_k(h, ctypes.byref(P), ctypes.byref(rep), _stream(stream))
     del keep
@@ -254,7 +260,7 @@ def eig_update_batch(h, problems, stream=None):
     keep = []
     for i, p in enumerate(problems):
         P, sb = _problem(p["Q"], p["lam"], p["K"], p.get("sigma"),
-                         p.get("want", EIG_VALUES | EIG_VECTORS), p.get("Q_out"))
+                         p.get("want", EIG_VALUES | EIG_VECTORS), p.get("Q_out"), p.get("errors"))
         arr[i] = P
         keep.append(sb)
     tickets = (ctypes.c_uint64 * max(1, len(problems)))()

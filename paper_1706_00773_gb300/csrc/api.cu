@@ -274,6 +274,7 @@ struct Table {
   long long total_cols = 0, total_copy = 0;
   int64_t max_n = 0;
   int total_rb = 0, total_sl = 0, total_gt = 0;
+  bool any_errors = false;  // some update wants the per-eigenpair report
   // report (single update only)
   double* chk_tmp = nullptr;
   double* chk_out = nullptr;
@@ -390,6 +391,8 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     d.Vr = reinterpret_cast<double*>(b.take(sizeof(double) * (size_t)n * k));
     d.taur = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
     d.runs = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
+    d.errors = vectors ? P->errors : nullptr;
+    if (d.errors) T.any_errors = true;
     if (n > T.max_n) T.max_n = n;
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
       d.lamf = reinterpret_cast<float2*>(b.take(sizeof(float2) * ld));
@@ -497,6 +500,10 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
     CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));
     nl += 3;
   }
+  if (vectors && T.any_errors) {
+    CK(launch_errors_gap_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
+    ++nl;
+  }
   MARK(5);
   if (vectors) {
     if (mixed) {
@@ -557,6 +564,9 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->iters_max = st.iters_max;
   rep->n_notconv = st.n_notconv;
   rep->norm_A = st.lam_absmax + st.fro2;
+  rep->max_pair_residual = st.err_max[0];
+  rep->max_pair_rayleigh = st.err_max[1];
+  rep->max_pair_orth = st.err_max[2];
   if (chk) {
     const int nc = (int)(P->n < kCheckCols ? P->n : kCheckCols);
     double r = 0.0, o = 0.0;

@@ -50,6 +50,8 @@ struct DevStatus {
   long long taylor_total;  // evaluations by a first-order update of the K x K sums
   int n_runs;              // runs of exactly repeated lam rotated before deflation
   int run_rows;            // rows in those runs
+  double err_max[3];       // per-eigenpair report maxima: residual, Rayleigh shift,
+                           // next-vector dot (non-negative: atomicMax on the bits)
 };
 
 // The non-deflated sub-problem in the layout the secular kernels read.  Its
@@ -175,6 +177,7 @@ struct ProbDesc {
   double* Vr;              // reflectors of the runs of equal lam (n x k), see runs.cu
   double* taur;            // their scalars (n)
   int* runs;               // (g0, m) pairs (n ints)
+  double* errors;          // caller: n x 4 per-eigenpair report (column-major), or null
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
@@ -310,6 +313,10 @@ cudaError_t launch_perturb_w(int64_t n, int k, const double* lam, const double* 
                              bool transposed, double* W, cudaStream_t s);
 cudaError_t launch_perturb_mu(int64_t n, int k, const double* lam, const double* U, unsigned long long negmask,
                               double* mu, cudaStream_t s);
+// Column 2 (nearest-eigenvalue gap) of the per-eigenpair report of every
+// update of the table that asked for one; colpre: device prefix of n.
+cudaError_t launch_errors_gap_grouped(const ProbDesc* P, int count, const long long* colpre, long long total,
+                                      cudaStream_t s);
 // Small helpers (util.cu).
 cudaError_t launch_copy_guarded(double* dst, const double* src, int64_t count, const DevStatus* st,
                                 cudaStream_t s);

@@ -1459,13 +1459,31 @@ constexpr int kAsmCache = 32;
 // One CTA per secular root m: w_i = (u_i^T alpha) / (lam_i - mu), |w| = 1, the
 // entry of largest magnitude made positive, scattered to W[idx_i, pos].
 // One eq. (10) column: every thread of the CTA takes part (block reductions).
+// Sum over the CTA of one value per thread (every thread gets the sum); sh
+// holds kAsmThreads / 32 doubles and may be reused right after.
+__device__ __forceinline__ double block_sum_asm(double v, double* sh) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double a = 0.0;
+#pragma unroll
+  for (int w = 0; w < kAsmThreads / 32; ++w) a += sh[w];
+  return a;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  if (v >= 0.0) atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
 template <int K>
 __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roots, int64_t n,
                                               const double* __restrict__ lam_defl, int nd, int nk,
                                               const double* __restrict__ mu_sec,
                                               double* __restrict__ lam_out, double* __restrict__ W,
                                               const WSlices& ws, int m, double* s_n2, double* s_mx,
-                                              int* s_ix, int64_t pos_shift = 0) {
+                                              int* s_ix, int64_t pos_shift = 0, double* errs = nullptr,
+                                              DevStatus* stw = nullptr) {
   const int t = threadIdx.x;
   const double mu = mu_sec[m];
   const int64_t pos = m + lower_bound_d(lam_defl, nd, mu) - pos_shift;
@@ -1537,6 +1555,89 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
   __syncthreads();
   const double wmax = wcomp(imax);
   const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
+  if (errs) {
+    // Per-eigenpair report in FP64 on the unit vector w = scale * (eq. (10)
+    // entries), in the old eigenbasis, where A' is Lambda + U Sigma U^T:
+    //   r = (A' - mu) w,  r_i = (lam_i - mu) w_i + u_i^T Sigma s,  s = U^T w,
+    // |r| (metric (B) per pair) and w^T r = rho - mu (Rayleigh quotient).
+    // Deflated rows are outside the sub-problem (their u_i are below the
+    // deflation bound and add at most that much).
+    auto for_entries = [&](auto&& f) {
+      if (cached) {
+#pragma unroll
+        for (int c = 0; c < kAsmCache; ++c) {
+          const int i = t + c * kAsmThreads;
+          if (i < nk) f(i, wc[c] * scale);
+        }
+      } else {
+        for (int i = t; i < nk; i += kAsmThreads) f(i, wcomp(i) * scale);
+      }
+    };
+    double sp[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) sp[c] = 0.0;
+    for_entries([&](int i, double w) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) sp[c] = fma(sub.Us[(size_t)c * sub.ld + i], w, sp[c]);
+    });
+    double sv[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) sv[c] = sigma_of(sub.negmask, c) * block_sum_asm(sp[c], s_mx);
+    double r2 = 0.0, rw = 0.0;
+    for_entries([&](int i, double w) {
+      double r = ((sub.lam[i] - lam_o) - tau) * w;
+#pragma unroll
+      for (int c = 0; c < K; ++c) r = fma(sub.Us[(size_t)c * sub.ld + i], sv[c], r);
+      r2 = fma(r, r, r2);
+      rw = fma(r, w, rw);
+    });
+    r2 = block_sum_asm(r2, s_mx);
+    rw = block_sum_asm(rw, s_mx);
+    const double normA = sub.st->lam_absmax + sub.st->fro2;
+    // Orthogonality against the next root's vector where the two are close.
+    double dn = 0.0;
+    if (m + 1 < nk && mu_sec[m + 1] - mu <= 1e-6 * normA) {
+      const int m2 = m + 1;
+      const int o2 = roots.origin[m2];
+      const double tau2 = roots.tau[m2], lo2 = sub.lam[o2];
+      const int ia2 = roots.sidx[2 * (size_t)m2], ib2 = roots.sidx[2 * (size_t)m2 + 1];
+      const double wa2 = -roots.beta[2 * (size_t)m2], wb2 = -roots.beta[2 * (size_t)m2 + 1];
+      double al2[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) al2[c] = roots.alpha[(size_t)m2 * K + c];
+      double dd = 0.0, nn = 0.0;
+      for_entries([&](int i, double w) {
+        double v;
+        if (i == ia2) {
+          v = wa2;
+        } else if (i == ib2) {
+          v = wb2;
+        } else {
+          double ua = 0.0;
+#pragma unroll
+          for (int c = 0; c < K; ++c) ua = fma(sub.Us[(size_t)c * sub.ld + i], al2[c], ua);
+          v = ua / ((sub.lam[i] - lo2) - tau2);
+        }
+        dd = fma(w, v, dd);
+        nn = fma(v, v, nn);
+      });
+      dd = block_sum_asm(dd, s_mx);
+      nn = block_sum_asm(nn, s_mx);
+      dn = fabs(dd) / sqrt(nn);
+    }
+    if (t == 0) {
+      const double e0 = sqrt(r2) / normA, e1 = fabs(rw) / normA;
+      errs[pos] = e0;
+      errs[pos + n] = e1;
+      errs[pos + 3 * n] = dn;
+      if (stw) {
+        atomic_max_nonneg(&stw->err_max[0], e0);
+        atomic_max_nonneg(&stw->err_max[1], e1);
+        atomic_max_nonneg(&stw->err_max[2], dn);
+      }
+    }
+    __syncthreads();
+  }
   if (W) {
     double* col = W + pos * n;
     if (cached) {
@@ -1634,7 +1735,8 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_grouped_kernel(const Pro
     const Sub sub = sub_of(d);
     const WSlices ws = wslices_of(d, vectors && mixed);
     assemble_root<K>(sub, rootout_of(d), d.n, d.lam_defl, d.st->n_defl, *sub.n_dev, d.mu_sec, d.lam,
-                     (vectors && !mixed) ? d.W : nullptr, ws, item - c.pk[p], s_n2, s_mx, s_ix);
+                     (vectors && !mixed) ? d.W : nullptr, ws, item - c.pk[p], s_n2, s_mx, s_ix, 0,
+                     vectors ? d.errors : nullptr, d.st);
     __syncthreads();
   }
 }
@@ -1657,6 +1759,24 @@ __global__ void deflated_grouped_kernel(const ProbDesc* __restrict__ P, ClassDes
       const int lds = (d.n + 63) / 64 * 64;
       d.Ws[(size_t)pos * lds + d.idx_defl[j]] = __double2bfloat16(64.0);
       d.fcol[pos] = 2;
+    }
+    if (vectors && d.errors) {
+      // w = e_i: r = U Sigma u_i, |r| <= |U|_F |u_i| (the deflation bound),
+      // rho - mu = u_i^T Sigma u_i; e_i is orthogonal to every other vector.
+      const int i = d.idx_defl[j];
+      double un = 0.0, ray = 0.0;
+      for (int cc = 0; cc < d.k; ++cc) {
+        const double u = d.U[(size_t)cc * d.n + i];
+        un = fma(u, u, un);
+        ray = fma(sigma_of(d.negmask, cc) * u, u, ray);
+      }
+      const double normA = d.st->lam_absmax + d.st->fro2;
+      const double e0 = sqrt(d.st->fro2 * un) / normA, e1 = fabs(ray) / normA;
+      d.errors[pos] = e0;
+      d.errors[pos + d.n] = e1;
+      d.errors[pos + 3 * (int64_t)d.n] = 0.0;
+      atomic_max_nonneg(&d.st->err_max[0], e0);
+      atomic_max_nonneg(&d.st->err_max[1], e1);
     }
   }
 }

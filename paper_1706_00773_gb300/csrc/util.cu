@@ -74,7 +74,36 @@ __global__ void scatter_iters_kernel(Sub sub, int64_t n, const int* __restrict__
   }
 }
 
+// Column 2 of the per-eigenpair report: the distance of each new eigenvalue
+// to its nearest neighbour (over the whole spectrum, deflated pairs included),
+// relative to |A|.
+__global__ void errors_gap_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                          const long long* __restrict__ colpre) {
+  const long long total = colpre[count];
+  for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+       item += (long long)gridDim.x * blockDim.x) {
+    const int p = find_owner(colpre, count, item);
+    const ProbDesc& d = P[p];
+    if (!d.errors || (d.st->flags & (ST_UNSORTED | ST_NONFINITE))) continue;
+    const int64_t pos = item - colpre[p];
+    const double v = d.lam[pos];
+    double g = INFINITY;
+    if (pos > 0) g = v - d.lam[pos - 1];
+    if (pos + 1 < d.n) g = fmin(g, d.lam[pos + 1] - v);
+    d.errors[pos + 2 * (int64_t)d.n] = g / (d.st->lam_absmax + d.st->fro2);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_errors_gap_grouped(const ProbDesc* P, int count, const long long* colpre, long long total,
+                                      cudaStream_t s) {
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  errors_gap_grouped_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, count, colpre);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_copy_guarded(double* dst, const double* src, int64_t count, const DevStatus* st,
                                 cudaStream_t s) {
