@@ -191,9 +191,11 @@ def load_traffic(kernel: str):
         return None
 
 
-def cpu_baseline(P, sample: int, seed: int = 11):
+def cpu_baseline(P, sample: int, seed: int = 11, gpu=None):
     """The CPU oracle, as it stands, on a bounded sample of the same update:
-    `sample` roots spread over the spectrum, with their eq. (10) vectors."""
+    `sample` roots spread over the spectrum, with their eq. (10) vectors.
+    With gpu = (mu, X, norm_A) of the GPU's update, the sampled pairs also give
+    the GPU's error against the oracle, per eigenpair."""
     import numpy as np
 
     import oracle
@@ -206,9 +208,48 @@ def cpu_baseline(P, sample: int, seed: int = 11):
     out = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], sel=sel, nthreads=threads)
     dt = time.perf_counter() - t0
     assert out["X"].shape[1] == sample
-    return {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d of %d roots (bisection on the count) with eq. (10) vectors and X columns, "
-                      "one update of the benchmark workload; %.1f s" % (sample, n, dt)}
+    cb = {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+          "sample": "%d of %d roots (bisection on the count) with eq. (10) vectors and X columns, "
+                    "one update of the benchmark workload; %.1f s" % (sample, n, dt)}
+    if gpu is not None:
+        mu, X, normA = gpu
+        pos = out["pos"]
+        dmu = np.abs(mu[pos] - out["mu"]) / normA
+        cosv = np.abs(np.sum(X[:, pos] * out["X"], axis=0)) / (
+            np.linalg.norm(X[:, pos], axis=0) * np.linalg.norm(out["X"], axis=0))
+        gap = np.minimum(np.diff(out["mu"], prepend=-np.inf), np.diff(out["mu"], append=np.inf))
+        iso = gap > 1e-6 * normA  # eigenvectors are compared where they are determined
+        cb["vs_oracle"] = {"pairs": int(sample), "max_dmu_rel": float(np.max(dmu)),
+                           "p99_dmu_rel": float(np.percentile(dmu, 99)),
+                           "median_dmu_rel": float(np.median(dmu)),
+                           "max_sin_vec_isolated": float(np.sqrt(max(0.0, 1.0 - np.min(cosv[iso]) ** 2)))
+                           if iso.any() else None}
+    return cb
+
+
+def pair_error_report(eu, h, P, dev):
+    """One (untimed) update of the benchmark workload with the per-eigenpair
+    error report: max / p99 / median of its columns, and (mu, X, norm_A) for
+    the comparison against the oracle's sample."""
+    import numpy as np
+    import torch
+
+    n = P["lam"].shape[0]
+    Q = torch.from_numpy(np.asfortranarray(P["Q"])).to(dev)
+    lam = torch.from_numpy(P["lam"].copy()).to(dev)
+    K = torch.from_numpy(np.asfortranarray(P["K"])).to(dev)
+    X = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    E = torch.empty((4, n), dtype=torch.float64, device=dev).t()
+    rc, rep = eu.eig_update_rank_k(h, Q, lam, K, P["sigma"], eu.EIG_VALUES | eu.EIG_VECTORS, Q_out=X, errors=E)
+    torch.cuda.synchronize()
+    e = E.cpu().numpy()
+    st = lambda v: {"max": float(np.max(v)), "p99": float(np.percentile(v, 99)), "median": float(np.median(v))}
+    out = {"status": rc, "residual_rel": st(e[:, 0]), "rayleigh_rel": st(e[:, 1]),
+           "next_vector_dot": st(e[:, 3]), "min_gap_rel": float(np.min(e[:, 2])),
+           "how": "eig_problem.errors of one update (FP64 eq. (10) vectors in the old eigenbasis)"}
+    gpu = (lam.cpu().numpy(), X.cpu().numpy(), float(rep["norm_A"]))
+    del Q, K, X, E
+    return out, gpu
 
 
 def run_reference(args):
@@ -573,6 +614,7 @@ def main():
     R = run_mode(eu, h, P, dev, args.steps, args.warmup, world)
     clk = clocks.stop()
     reps = R["reps"]
+    pair_errors, gpu_pairs = pair_error_report(eu, h, P, dev)
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e_value = None
@@ -773,7 +815,7 @@ def main():
         "comparisons": comparisons, "roofline_other": other, "roots_fp32": roots_fp32,
         "batched": batched, "serving": serving, "k_sweep": k_sweep,
         "fp64_fma_rate": {"gflops": fp64_meas, "clocks": fp64_clk},
-        "e2e_how": e2e_note, "serial_update_with_copies_ms": e2e_serial_ms,
+        "pair_errors": pair_errors, "e2e_how": e2e_note, "serial_update_with_copies_ms": e2e_serial_ms,
         "evals_per_root": evals / max(1, n_keep), "fp32_evals_per_root": evals32 / max(1, n_keep),
         "first_order_updates_per_root": taylor / max(1, n_keep)}}
     summ = lambda d, keys: ({kk: d.get(kk) for kk in keys} if d else None)
@@ -791,12 +833,18 @@ def main():
             "batched": summ(batched, ("value", "ms_per_step", "updates_per_step", "failed_updates",
                                       "max_err_vs_oracle", "tuned_vs_untuned")),
             "serving": summ(serving, ("value", "latency_ms", "residents", "requests", "drift_vs_oracle")),
+            "pair_errors": {"residual_rel": pair_errors["residual_rel"],
+                            "rayleigh_max": pair_errors["rayleigh_rel"]["max"],
+                            "next_dot_max": pair_errors["next_vector_dot"]["max"],
+                            "vs_oracle": pair_errors.get("vs_oracle")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(r["launches"] for r in reps)),
             "roofline": {kk: v for kk, v in dominant.items() if kk not in ("peak_source", "work")},
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(P, args.cpu_sample)
+        cb = cpu_baseline(P, args.cpu_sample, gpu=gpu_pairs)
+        pair_errors["vs_oracle"] = cb.pop("vs_oracle", None)
+        line["pair_errors"]["vs_oracle"] = pair_errors["vs_oracle"]
         detail["bench_detail"]["cpu_baseline_sample"] = cb["sample"]
         cb["sample"] = cb["sample"].split(";")[0]
         line["cpu_baseline"] = cb

@@ -84,6 +84,23 @@ struct RootOut {
   int* sidx;        // 2 per root: indices of the bracketing poles (-1: none)
 };
 
+// Reciprocal of d to within about one ulp, cheaper on the FP64 pipe than the
+// correctly rounded division: the hardware's fast approximation y0 =
+// rcp.approx.ftz.f64(d), refined by one step of the cubically convergent
+// Newton-Raphson iteration for f(y) = 1/y - d,
+//   e = 1 - d y0,  y1 = y0 (1 + e + e^2)   (the series of 1/(1 - e) truncated),
+// so the relative error of y0 is cubed.  d with a zero, subnormal, infinite
+// or NaN exponent field goes through the division (checked on the integer
+// pipe), so the result equals 1/d's special cases.
+__device__ __forceinline__ double rcp_nr(double d) {
+  const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7ffu;
+  if (ex == 0u || ex >= 0x7feu) return 1.0 / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
 // ---- split-BF16 tensor-core GEMM (gemm_tc.cu) ------------------------------
 constexpr int kTcSlices = 5;
 
