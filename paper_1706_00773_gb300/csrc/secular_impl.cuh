@@ -221,115 +221,6 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
                                                  skip_b, sA, sB, lane, Usf);
 }
 
-// The zero finder's sums for a root owned by E > 1 warps (K >= 10).  The warps
-// split the K x K entries but all need every term's reciprocal r_i = 1/(x -
-// lam_i): each is formed once, by the warp whose slot of the current chunk of
-// 32 E terms holds it, and passed through shared memory (sR doubles and, for
-// ACC_MN32, sRf floats: two buffers of 32 E each, one group barrier per chunk).
-// Same sums as accumulate<K, E, e, MODE> (ACC_MN or ACC_MN32), same order of
-// the additions within each lane.
-template <int K, int E, int e, int MODE>
-__device__ __forceinline__ void accumulate_sr(const double* __restrict__ lam, const double* __restrict__ Us,
-                                              int ld, int n, double lam_o, double tau, int skip_a, int skip_b,
-                                              double* sA, double* sB, int lane, int g, double* sR, float* sRf,
-                                              const float* __restrict__ Usf) {
-  static_assert(MODE == ACC_MN || MODE == ACC_MN32, "zero-finder sums only");
-  constexpr int NS = nslots<K, E, e>();
-  constexpr int KP = K + 1;
-  constexpr int CH = 32 * E;
-  using BT = typename pick_type<MODE == ACC_MN32, float, double>::type;
-  double A[NS];
-  BT B[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    A[s] = 0.0;
-    B[s] = (BT)0;
-  }
-  int buf = 0;
-  for (int base = 0; base < n; base += CH) {
-    const int i0 = base + e * 32 + lane;
-    double r0 = 0.0;
-    if (i0 < n && i0 != skip_a && i0 != skip_b) r0 = rcp_nr(tau - (__ldg(lam + i0) - lam_o));
-    sR[buf * CH + e * 32 + lane] = r0;
-    if (MODE == ACC_MN32) sRf[buf * CH + e * 32 + lane] = (float)r0;
-    group_sync<E>(g);
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-      const int i = base + j * 32 + lane;
-      if (i < n) {
-        const double r = sR[buf * CH + j * 32 + lane];
-        double u[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) u[c] = __ldg(Us + (size_t)c * ld + i);
-        double t[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) t[c] = u[c] * r;
-        float tf[K];
-        if (MODE == ACC_MN32) {
-          const float rf = sRf[buf * CH + j * 32 + lane];
-#pragma unroll
-          for (int c = 0; c < K; ++c) tf[c] = __ldg(Usf + (size_t)c * ld + i) * rf;
-        }
-        int s = 0;
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-          if (owner_of<K, E>(a) == e) {
-#pragma unroll
-            for (int b = a; b < K; ++b) {
-              A[s] = fma(t[a], u[b], A[s]);
-              if (MODE == ACC_MN) B[s] = (BT)fma(t[a], t[b], (double)B[s]);
-              if (MODE == ACC_MN32) B[s] = (BT)fmaf(tf[a], tf[b], (float)B[s]);
-              ++s;
-            }
-          }
-        }
-      }
-    }
-    buf ^= 1;
-  }
-  double B64[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    A[s] = warp_sum(A[s]);
-    B64[s] = (MODE == ACC_MN32) ? (double)warp_sum_f((float)B[s]) : warp_sum((double)B[s]);
-  }
-  if (lane == 0) {
-    int s = 0;
-#pragma unroll
-    for (int a = 0; a < K; ++a) {
-      if (owner_of<K, E>(a) == e) {
-#pragma unroll
-        for (int b = a; b < K; ++b) {
-          sA[a * KP + b] = A[s];
-          sA[b * KP + a] = A[s];
-          sB[a * KP + b] = B64[s];
-          sB[b * KP + a] = B64[s];
-          ++s;
-        }
-      }
-    }
-  }
-}
-
-template <int K, int E, int MODE>
-__device__ __forceinline__ void accumulate_sr_group(int e, const double* __restrict__ lam,
-                                                    const double* __restrict__ Us, int ld, int n, double lam_o,
-                                                    double tau, int skip_a, int skip_b, double* sA, double* sB,
-                                                    int lane, int g, double* sR, float* sRf,
-                                                    const float* __restrict__ Usf) {
-  if (E == 1 || e == 0)
-    accumulate_sr<K, E, 0, MODE>(lam, Us, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, g, sR, sRf, Usf);
-  else if (E > 1 && e == 1)
-    accumulate_sr<K, E, (E > 1 ? 1 : 0), MODE>(lam, Us, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, g, sR,
-                                               sRf, Usf);
-  else if (E > 2 && e == 2)
-    accumulate_sr<K, E, (E > 2 ? 2 : 0), MODE>(lam, Us, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, g, sR,
-                                               sRf, Usf);
-  else
-    accumulate_sr<K, E, (E > 3 ? 3 : 0), MODE>(lam, Us, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, g, sR,
-                                               sRf, Usf);
-}
-
 // ----------------------------------------------------------------------------
 // FP32 accumulation for the coarse phase of the zero finder (mixed mode).
 // The same sums as ACC_MN with x - lam_i formed from (hi, lo) float pairs as
@@ -475,7 +366,10 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
-    if (off == 0.0 || off <= 1e-36 * dia) break;
+    // Converged when the off-diagonal part is 1e-16 of the diagonal (Frobenius):
+    // it then moves no eigenvalue by more than that (Weyl), below the
+    // rotations' own rounding.
+    if (off == 0.0 || off <= 1e-32 * dia) break;
     for (int rnd = 0; rnd < M - 1; ++rnd) {
       int pj = 0, qj = 0;
       double cj = 1.0, sj = 0.0;
@@ -494,7 +388,7 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
         if (qj < K) {
           const double apq = A[pj * KP + qj], app = A[pj * KP + pj], aqq = A[qj * KP + qj];
           if (apq != 0.0) {
-            if (sweep > 2 && fabs(apq) * 1e18 < fabs(app) && fabs(apq) * 1e18 < fabs(aqq)) {
+            if (fabs(apq) * 1e18 < fabs(app) && fabs(apq) * 1e18 < fabs(aqq)) {
               A[pj * KP + qj] = 0.0;  // negligible against both diagonal entries
               A[qj * KP + pj] = 0.0;
             } else {
@@ -522,6 +416,9 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
         }
       }
       __syncwarp();
+      // A round whose pairs all need no rotation (warm starts converge to
+      // that within a sweep or two) skips the column and row passes.
+      if (__ballot_sync(0xffffffffu, act) == 0u) continue;
       // columns: A <- A J
 #pragma unroll
       for (int base = 0; base < ITEMS; base += 32) {
@@ -980,7 +877,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
                                            double* sVg, double* s_tau, double* s_lamo,
                                            int* s_done, int* s_ia, int* s_ib, int* s_ph,
                                            double* s_err, int* s_tay, double* s_step, int g, int e,
-                                           int lane, double* sR, float* sRf) {
+                                           int lane) {
   constexpr int E = warps_per_root(K);
   constexpr int KP = K + 1;
   constexpr int Z2 = K + 2;
@@ -1063,12 +960,6 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const float ho = (float)lam_o, th32 = (float)tau_c;
       accumulate32_group<K, E, true>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
                                (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
-    } else if (E > 1 && sub.Usf) {
-      accumulate_sr_group<K, E, ACC_MN32>(e, lam, Us, ld, n, lam_o, tau_c, skip_a, skip_b, sMg, sNg, lane, g, sR,
-                                          sRf, sub.Usf);
-    } else if (E > 1) {
-      accumulate_sr_group<K, E, ACC_MN>(e, lam, Us, ld, n, lam_o, tau_c, skip_a, skip_b, sMg, sNg, lane, g, sR,
-                                        sRf, nullptr);
     } else if (sub.Usf) {
       accumulate_group<K, E, ACC_MN32>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b, sMg, sNg,
                                        lane, sub.Usf);
@@ -1472,8 +1363,6 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   __shared__ double s_tau[G], s_lamo[G];
   __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
   __shared__ double s_err[G][2], s_step[G];
-  __shared__ double sR[G][E > 1 ? 64 * E : 1];
-  __shared__ float sRf[G][E > 1 ? 64 * E : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   if (input_invalid(sub.st)) return;
@@ -1485,8 +1374,7 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
     const int m = s_m[g];
     if (m >= stop) break;
     root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
-                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane,
-                  sR[g], sRf[g]);
+                  &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }
 
@@ -1503,8 +1391,6 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
   __shared__ double s_tau[G], s_lamo[G];
   __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
   __shared__ double s_err[G][2], s_step[G];
-  __shared__ double sR[G][E > 1 ? 64 * E : 1];
-  __shared__ float sRf[G][E > 1 ? 64 * E : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = warp / E, e = warp - (warp / E) * E;
   const int total = c.pk[c.count];
@@ -1522,7 +1408,7 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
     const Sub sub = sub_of(d);
     root_solve<K>(sub, d.pole_cnt, max_iter, rootout_of(d), d.st, *sub.n_dev, item - c.pk[p],
                   sM[g], sN[g], sZ[g], sV[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
-                  &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane, sR[g], sRf[g]);
+                  &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }
 
