@@ -293,6 +293,8 @@ int eig_pole_counts(eig_handle h, int64_t n, int32_t k, const double* lambda, co
  *     streams or two host threads at once) race and give wrong results.
  *   - The first call on a device looks up the array's device address (set-up,
  *     with that device current); make that first call before any stream capture.
+ *     The address is kept with the device's context: after cudaDeviceReset the
+ *     next call on that device does the set-up again.
  * Arguments as eig_secular_values (device lambda, U, mu, iters; host sigma),
  * plus max_iter (0 = 128).  Synchronises `stream` before returning. */
 #define EIG_STATIC_MAX_N 8192

@@ -144,13 +144,6 @@ struct DeviceGuard {
   }
 };
 
-int status_of(const DevStatus& s) {
-  if (s.flags & (ST_UNSORTED | ST_NONFINITE)) return EIG_EINVAL;
-  if (s.flags & ST_TIMEOUT) return EIG_ETIMEOUT;
-  if (s.flags & ST_NOTCONV) return EIG_ENOTCONV;
-  return EIG_OK;
-}
-
 }  // namespace
 
 struct eig_ctx {
@@ -199,24 +192,6 @@ int ensure_ws(eig_ctx* h, size_t bytes) {
   h->ws_bytes = bytes;
   ++h->m_allocs;
   return EIG_OK;
-}
-
-bool sigma_info(const int8_t* sigma, int k, unsigned long long* negmask, int* kplus) {
-  unsigned long long m = 0;
-  int kp = 0;
-  for (int c = 0; c < k; ++c) {
-    const int v = sigma ? sigma[c] : 1;
-    if (v == 1) {
-      ++kp;
-    } else if (v == -1) {
-      m |= 1ull << c;
-    } else {
-      return false;
-    }
-  }
-  *negmask = m;
-  *kplus = kp;
-  return true;
 }
 
 #define CK(x)                         \

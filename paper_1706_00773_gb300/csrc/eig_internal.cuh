@@ -54,6 +54,35 @@ struct DevStatus {
                            // next-vector dot (non-negative: atomicMax on the bits)
 };
 
+// Public status of a finished update from its device status block (shared by
+// every entry point, so that they map the flags the same way).
+inline int status_of(const DevStatus& s) {
+  if (s.flags & (ST_UNSORTED | ST_NONFINITE)) return EIG_EINVAL;
+  if (s.flags & ST_TIMEOUT) return EIG_ETIMEOUT;
+  if (s.flags & ST_NOTCONV) return EIG_ENOTCONV;
+  return EIG_OK;
+}
+
+// sigma (host k entries of +1/-1, NULL = all +1) as the bit mask of the -1
+// columns and the number of +1 columns; false for any other entry.
+inline bool sigma_info(const int8_t* sigma, int k, unsigned long long* negmask, int* kplus) {
+  unsigned long long m = 0;
+  int kp = 0;
+  for (int c = 0; c < k; ++c) {
+    const int v = sigma ? sigma[c] : 1;
+    if (v == 1) {
+      ++kp;
+    } else if (v == -1) {
+      m |= 1ull << c;
+    } else {
+      return false;
+    }
+  }
+  *negmask = m;
+  *kplus = kp;
+  return true;
+}
+
 // The non-deflated sub-problem in the layout the secular kernels read.  Its
 // size n' is only known on the device (written by the deflation kernel), so
 // kernels read it through n_dev and are launched for the worst case ld.

@@ -21,7 +21,11 @@
 //     race on the array and give wrong results: serialise them;
 //   - the first call on a device does the set-up (looks up the array's device
 //     address with cudaGetSymbolAddress, with that device current); make that
-//     first call before any stream capture.
+//     first call before any stream capture.  The address is kept together
+//     with the device's current context: after cudaDeviceReset (which
+//     reloads the module, so the array may move) the next call sees a new
+//     context and does the set-up again instead of using a stale address.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,7 +43,25 @@ static __device__ __align__(256) unsigned char g_eig_scratch[kStaticBytes];
 
 std::mutex g_mu;
 void* g_scratch_dev[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
+
+// cuCtxGetCurrent from the driver, through the runtime (no link-time
+// dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
 
 constexpr size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -62,8 +84,17 @@ int scratch_for_current_device(char** base, int* num_sms) {
     cudaGetLastError();
     return EIG_ECUDA;
   }
+  // The device's context (cudaSetDevice initialises it when needed): the
+  // cached address belongs to the context it was looked up in.
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    return EIG_ECUDA;
+  }
+  CtxGetCurrentFn get_ctx = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return EIG_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_dev[dev]) {
+  if (!g_scratch_dev[dev] || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_eig_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -75,6 +106,7 @@ int scratch_for_current_device(char** base, int* num_sms) {
       return EIG_ECUDA;
     }
     g_scratch_dev[dev] = p;
+    g_scratch_ctx[dev] = ctx;
     g_sms[dev] = sms;
   }
   *base = static_cast<char*>(g_scratch_dev[dev]);
@@ -99,12 +131,7 @@ extern "C" int eig_secular_values_static(int64_t n, int32_t k, const double* lam
   if (n > EIG_STATIC_MAX_N || k > EIG_MAX_K) return EIG_ETOOBIG;
   unsigned long long negmask = 0;
   int kplus = 0;
-  for (int c = 0; c < k; ++c) {
-    const int v = sigma ? sigma[c] : 1;
-    if (v == 1) ++kplus;
-    else if (v == -1) negmask |= 1ull << c;
-    else return EIG_EINVAL;
-  }
+  if (!sigma_info(sigma, k, &negmask, &kplus)) return EIG_EINVAL;
   char* base = nullptr;
   int num_sms = 0;
   int rc = scratch_for_current_device(&base, &num_sms);
@@ -166,7 +193,5 @@ extern "C" int eig_secular_values_static(int64_t n, int32_t k, const double* lam
   DevStatus host_st;
   CKS(cudaMemcpyAsync(&host_st, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   CKS(cudaStreamSynchronize(s));
-  if (host_st.flags & (ST_UNSORTED | ST_NONFINITE)) return EIG_EINVAL;
-  if (host_st.flags & ST_NOTCONV) return EIG_ENOTCONV;
-  return EIG_OK;
+  return status_of(host_st);
 }

@@ -563,6 +563,94 @@ __device__ void warp_jacobi_f32(float* A, float* V, int lane) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// Inverse of an N x N matrix Z (row stride N+1, shared memory, left intact) by
+// Gauss-Jordan elimination with partial pivoting, one warp: A is the working
+// copy, B receives Z^{-1}.  Lane c owns column c of A and of B (N <= 32);
+// each row's elimination factor is broadcast from the lane that read it, so
+// no factor is overwritten before use.  Returns false (B invalid)
+// if a pivot is zero or not finite.  *detneg = 1 when det Z < 0 (pivot signs
+// and row swaps); *zf = |Z|_F, *bf = |Z^{-1}|_F, *bkf = |(Z^{-1})_{KK}|_F (the
+// leading KB x KB block).
+// ----------------------------------------------------------------------------
+template <int N>
+__device__ bool warp_gj_inverse(const double* Z, double* A, double* B, int lane, int KB, int* detneg,
+                                double* zf, double* bf, double* bkf) {
+  constexpr int P = N + 1;
+  double z2 = 0.0;
+  for (int idx = lane; idx < N * N; idx += 32) {
+    const int r = idx / N, c = idx - (idx / N) * N;
+    const double v = Z[r * P + c];
+    A[r * P + c] = v;
+    B[r * P + c] = (r == c) ? 1.0 : 0.0;
+    z2 = fma(v, v, z2);
+  }
+  z2 = warp_sum(z2);
+  __syncwarp();
+  int neg = 0;
+  for (int j = 0; j < N; ++j) {
+    double v = (lane >= j && lane < N) ? fabs(A[lane * P + j]) : -1.0;
+    int ir = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, ir, off);
+      if (ov > v || (ov == v && oi < ir)) {
+        v = ov;
+        ir = oi;
+      }
+    }
+    if (!(v > 0.0) || !(v < INFINITY)) return false;  // warp-uniform
+    if (ir != j) {
+      if (lane < N) {
+        const double a0 = A[j * P + lane], a1 = A[ir * P + lane];
+        A[j * P + lane] = a1;
+        A[ir * P + lane] = a0;
+        const double b0 = B[j * P + lane], b1 = B[ir * P + lane];
+        B[j * P + lane] = b1;
+        B[ir * P + lane] = b0;
+      }
+      neg ^= 1;
+      __syncwarp();
+    }
+    const double pv = A[j * P + j];
+    if (pv < 0.0) neg ^= 1;
+    const double rp = 1.0 / pv;
+    const double f = (lane < N) ? A[lane * P + j] : 0.0;  // factor of row `lane`
+    __syncwarp();
+    if (lane < N) {
+      A[j * P + lane] *= rp;
+      B[j * P + lane] *= rp;
+    }
+    __syncwarp();
+    const double aj0 = (lane < N) ? A[j * P + lane] : 0.0;
+    const double bj0 = (lane < N) ? B[j * P + lane] : 0.0;
+#pragma unroll 2
+    for (int r = 0; r < N; ++r) {
+      const double fr = __shfl_sync(0xffffffffu, f, r);
+      if (r != j && lane < N) {
+        A[r * P + lane] = fma(-fr, aj0, A[r * P + lane]);
+        B[r * P + lane] = fma(-fr, bj0, B[r * P + lane]);
+      }
+    }
+    __syncwarp();
+  }
+  double i2 = 0.0, ik2 = 0.0;
+  for (int idx = lane; idx < N * N; idx += 32) {
+    const int r = idx / N, c = idx - (idx / N) * N;
+    const double b = B[r * P + c];
+    i2 = fma(b, b, i2);
+    if (r < KB && c < KB) ik2 = fma(b, b, ik2);
+  }
+  i2 = warp_sum(i2);
+  ik2 = warp_sum(ik2);
+  *detneg = neg;
+  *zf = sqrt(z2);
+  *bf = sqrt(i2);
+  *bkf = sqrt(ik2);
+  return isfinite(i2);
+}
+
 __device__ __forceinline__ bool input_invalid(const DevStatus* st) {
   return (st->flags & (ST_UNSORTED | ST_NONFINITE)) != 0;
 }
@@ -874,7 +962,7 @@ template <int K>
 __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict__ pole_cnt,
                                            int max_iter, const RootOut& out, DevStatus* st, int n,
                                            int m, double* sMg, double* sNg, double* sZg,
-                                           double* sVg, double* s_tau, double* s_lamo,
+                                           double* sVg, double* sAg, double* sIg, double* s_tau, double* s_lamo,
                                            int* s_done, int* s_ia, int* s_ib, int* s_ph,
                                            double* s_err, int* s_tay, double* s_step, int g, int e,
                                            int lane) {
@@ -893,6 +981,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   bool has_a = false, has_b = false, first = false, notconv = false;
   double tl = 0.0, th = 0.0, tau = 0.0, da = 0.0, db = 0.0, prev_step = INFINITY;
   bool last_model = false;  // the current point came from a two-pole model step
+  bool vvalid = false;      // V holds eigenvectors of an earlier Z (Jacobi warm start)
   if (e == 0) {
     int lo = 0, hi = n;  // p = #{q : pole_cnt[q] <= m}
     while (lo < hi) {
@@ -991,123 +1080,170 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
         Z[r * ZP + c] = v;
       }
       __syncwarp();
-      if (it > 0) {
-        // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
-        // then let Jacobi finish and accumulate onto V.  T = Z V, then V^T T,
-        // each entry by one lane (all 32 lanes busy), T kept in Z's storage.
-        constexpr int ZE = Z2 * Z2;
-        constexpr int NB = (ZE + 31) / 32;
-        double tv[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const int idx = b * 32 + lane;
-          double acc = 0.0;
-          if (idx < ZE) {
-            const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
-            for (int q = 0; q < Z2; ++q) acc = fma(Z[r * ZP + q], V[q * ZP + c], acc);
+      // Eigen-decomposition of Z (parallel Jacobi, warm-started from the last
+      // one's eigenvectors when there is one); Z's diagonal then holds the
+      // eigenvalues and V the eigenvectors.
+      auto diag_Z = [&]() {
+        if (vvalid) {
+          // Warm start: rotate Z into the previous eigenbasis (nearly diagonal),
+          // then let Jacobi finish and accumulate onto V.  T = Z V, then V^T T,
+          // each entry by one lane (all 32 lanes busy), T kept in Z's storage.
+          constexpr int ZE = Z2 * Z2;
+          constexpr int NB = (ZE + 31) / 32;
+          double tv[NB];
+  #pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const int idx = b * 32 + lane;
+            double acc = 0.0;
+            if (idx < ZE) {
+              const int r = idx / Z2, c = idx - (idx / Z2) * Z2;
+              for (int q = 0; q < Z2; ++q) acc = fma(Z[r * ZP + q], V[q * ZP + c], acc);
+            }
+            tv[b] = acc;
           }
-          tv[b] = acc;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const int idx = b * 32 + lane;
-          if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const int idx = b * 32 + lane;
-          double acc = 0.0;
-          if (idx < ZE) {
-            const int i = idx / Z2, c = idx - (idx / Z2) * Z2;
-            for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], Z[r * ZP + c], acc);
+          __syncwarp();
+  #pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const int idx = b * 32 + lane;
+            if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
           }
-          tv[b] = acc;
+          __syncwarp();
+  #pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const int idx = b * 32 + lane;
+            double acc = 0.0;
+            if (idx < ZE) {
+              const int i = idx / Z2, c = idx - (idx / Z2) * Z2;
+              for (int r = 0; r < Z2; ++r) acc = fma(V[r * ZP + i], Z[r * ZP + c], acc);
+            }
+            tv[b] = acc;
+          }
+          __syncwarp();
+  #pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const int idx = b * 32 + lane;
+            if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
+          }
+          __syncwarp();
+          if (lane < Z2) {  // exact symmetry
+            for (int i = lane + 1; i < Z2; ++i) Z[i * ZP + lane] = Z[lane * ZP + i];
+          }
+          __syncwarp();
+          warp_jacobi<Z2>(Z, V, lane, false);
+        } else {
+          warp_jacobi<Z2>(Z, V, lane, true);
         }
-        __syncwarp();
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          const int idx = b * 32 + lane;
-          if (idx < ZE) Z[(idx / Z2) * ZP + (idx - (idx / Z2) * Z2)] = tv[b];
-        }
-        __syncwarp();
-        if (lane < Z2) {  // exact symmetry
-          for (int i = lane + 1; i < Z2; ++i) Z[i * ZP + lane] = Z[lane * ZP + i];
-        }
-        __syncwarp();
-        warp_jacobi<Z2>(Z, V, lane, false);
-      } else {
-        warp_jacobi<Z2>(Z, V, lane, true);
-      }
-      // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]);
-      // G = (Z^{-1})_{SS} for the two-pole model below.
-      double zj = 0.0, contrib = 0.0, g11 = 0.0, g12 = 0.0, g22 = 0.0;
-      if (lane < Z2) {
-        zj = Z[lane * ZP + lane];
-        double q = 0.0;
-        for (int a = 0; a < K; ++a) {
-          double na = 0.0;
-          for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
-          q = fma(V[a * ZP + lane], na, q);
-        }
-        const double za = V[K * ZP + lane], zb = V[(K + 1) * ZP + lane];
-        if (has_a) q = fma(za, za, q);
-        if (has_b) q = fma(zb, zb, q);
-        const double rz = 1.0 / zj;
-        contrib = q * rz;
-        g11 = za * za * rz;
-        g12 = za * zb * rz;
-        g22 = zb * zb * rz;
-      }
-      const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
-      const double tsum = warp_sum(contrib);
-      g11 = warp_sum(g11);
-      g12 = warp_sum(g12);
-      g22 = warp_sum(g22);
+        vvalid = true;
+      };
       const int posD = (Da > 0.0 ? 1 : 0) + (Db > 0.0 ? 1 : 0);
       // Inside the bracket #{lam_i < x} is the pole index p.
       below = has_a ? p : 0;
-      const int count = below + __popc(posmask) - posD - sub.kplus;
-      // FP32 phase: the count is exact when no eigenvalue of Z can change sign
-      // under the error of the FP32 sums, which only enters the K x K block:
-      //   E = |dM^|_2 <= (L + 16) 2^-24 S1 + 2^-46 max|lam| S2   (L terms per lane,
-      //   three roundings per term, five in the warp's FP32 butterfly, slack),
-      // plus the Jacobi's own rounding.  Eigenvalues with |z_j| > 2E keep their
-      // sign (Weyl).  The small ones belong to eigenvectors that live almost
-      // entirely in the two bordered rows; with s the small set, W = |V_{K,s}|_F^2
-      // (their weight in the K block) and g the distance of the large ones from
-      // zero, each small eigenvalue moves by at most E W + E^2 W / g (a
-      // Hermitian block perturbation with the large block eliminated).  If any
-      // sign is not certain this point is evaluated again in FP64 and the FP64
-      // phase takes over.
+      double tsum = 0.0, g11 = 0.0, g12 = 0.0, g22 = 0.0;
+      int count = 0;
       bool redo = false, conv = false;
-      if (ph32) {
-        const bool nonfin = __any_sync(0xffffffffu, lane < Z2 && !isfinite(zj));
-        double zmax = (lane < Z2) ? fabs(zj) : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
-        const double L = (double)((n + 31) / 32);
-        const double E = 1.25 * ((L + 16.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
-                         64.0 * kEps * zmax;
-        const bool small = lane < Z2 && !(fabs(zj) > 2.0 * E);
-        double wk = 0.0;
-        if (small) {
-          for (int c = 0; c < K; ++c) wk = fma(V[c * ZP + lane], V[c * ZP + lane], wk);
+      // One root in the bracket (the common case): the count is c_lo or c_hi,
+      // and it follows from the sign of det Z alone -- neg(Z) has the parity of
+      // [det Z < 0], so count = below + (Z2 - neg(Z)) - posD - k_plus is known
+      // mod 2.  Z^{-1} (Gauss-Jordan, no eigen-decomposition) gives the Newton
+      // step p'/p = tr(Z^{-1} Z'), Z' = diag(N^, [a], [b]), and the model's
+      // G = (Z^{-1})_SS.  FP32 phase: the FP32 sums' error Delta sits in the
+      // K x K block (|Delta|_2 <= E); Z + t Delta = Z (I + t Z^{-1} Delta) stays
+      // nonsingular for t in [0, 1] when E |(Z^{-1})_KK|_2 < 1, so det Z keeps
+      // its sign and the count is certified; with the Gauss-Jordan rounding
+      // (64 Z2 eps |Z|_F |Z^{-1}|_F) the test below keeps a factor-2 margin.
+      bool gj = false;
+      if (c_hi - c_lo == 1) {
+        int detneg = 0;
+        double zf = 0.0, invf = 0.0, invkf = 0.0;
+        gj = warp_gj_inverse<Z2>(Z, sAg, sIg, lane, K, &detneg, &zf, &invf, &invkf);
+        if (gj) {
+          const double* Inv = sIg;
+          double q = 0.0;
+          for (int idx = lane; idx < K * K; idx += 32) {
+            const int r = idx / K, c = idx - (idx / K) * K;
+            q = fma(Inv[r * ZP + c], Nm[c * KP + r], q);
+          }
+          q = warp_sum(q);
+          g11 = Inv[K * ZP + K];
+          g12 = Inv[K * ZP + K + 1];
+          g22 = Inv[(K + 1) * ZP + K + 1];
+          tsum = q + (has_a ? g11 : 0.0) + (has_b ? g22 : 0.0);
+          const int par = (below + Z2 - detneg - posD - sub.kplus) & 1;
+          count = ((c_lo & 1) == par) ? c_lo : c_hi;
+          if (ph32) {
+            const double L = (double)((n + 31) / 32);
+            const double Es = 1.25 * ((L + 16.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]);
+            redo = !(Es * invkf + 64.0 * Z2 * kEps * zf * invf < 0.5) || !isfinite(tsum);
+          }
         }
-        double zs = small ? fabs(zj) : INFINITY;
-        double zb = (lane < Z2 && !small) ? fabs(zj) : INFINITY;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          wk += __shfl_xor_sync(0xffffffffu, wk, off);
-          zs = fmin(zs, __shfl_xor_sync(0xffffffffu, zs, off));
-          zb = fmin(zb, __shfl_xor_sync(0xffffffffu, zb, off));
+      }
+      if (!gj) {
+        diag_Z();
+        // p'/p = sum_j z_j^T Z' z_j / zeta_j,  Z' = diag(N^, [a real], [b real]);
+        // G = (Z^{-1})_{SS} for the two-pole model below.
+        double zj = 0.0, contrib = 0.0;
+        if (lane < Z2) {
+          zj = Z[lane * ZP + lane];
+          double q = 0.0;
+          for (int a = 0; a < K; ++a) {
+            double na = 0.0;
+            for (int b = 0; b < K; ++b) na = fma(Nm[a * KP + b], V[b * ZP + lane], na);
+            q = fma(V[a * ZP + lane], na, q);
+          }
+          const double za = V[K * ZP + lane], zb = V[(K + 1) * ZP + lane];
+          if (has_a) q = fma(za, za, q);
+          if (has_b) q = fma(zb, zb, q);
+          const double rz = 1.0 / zj;
+          contrib = q * rz;
+          g11 = za * za * rz;
+          g12 = za * zb * rz;
+          g22 = zb * zb * rz;
         }
-        const double g = zb - E;
-        const double shift = E * wk + E * E * wk / g;
-        const bool any_small = zs < INFINITY;
-        redo = nonfin || !(E < INFINITY) ||
-               (any_small && !(g > 0.0 && zs > 2.0 * shift + 64.0 * kEps * zmax));
+        const unsigned posmask = __ballot_sync(0xffffffffu, lane < Z2 && zj > 0.0);
+        tsum = warp_sum(contrib);
+        g11 = warp_sum(g11);
+        g12 = warp_sum(g12);
+        g22 = warp_sum(g22);
+        count = below + __popc(posmask) - posD - sub.kplus;
+        // FP32 phase: the count is exact when no eigenvalue of Z can change sign
+        // under the error of the FP32 sums, which only enters the K x K block:
+        //   E = |dM^|_2 <= (L + 16) 2^-24 S1 + 2^-46 max|lam| S2   (L terms per lane,
+        //   three roundings per term, five in the warp's FP32 butterfly, slack),
+        // plus the Jacobi's own rounding.  Eigenvalues with |z_j| > 2E keep their
+        // sign (Weyl).  The small ones belong to eigenvectors that live almost
+        // entirely in the two bordered rows; with s the small set, W = |V_{K,s}|_F^2
+        // (their weight in the K block) and g the distance of the large ones from
+        // zero, each small eigenvalue moves by at most E W + E^2 W / g (a
+        // Hermitian block perturbation with the large block eliminated).  If any
+        // sign is not certain this point is evaluated again in FP64 and the FP64
+        // phase takes over.
+        if (ph32) {
+          const bool nonfin = __any_sync(0xffffffffu, lane < Z2 && !isfinite(zj));
+          double zmax = (lane < Z2) ? fabs(zj) : 0.0;
+  #pragma unroll
+          for (int off = 16; off > 0; off >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
+          const double L = (double)((n + 31) / 32);
+          const double E = 1.25 * ((L + 16.0) * 0x1p-24 * s_err[0] + 0x1p-46 * sub.st->lam_absmax * s_err[1]) +
+                           64.0 * kEps * zmax;
+          const bool small = lane < Z2 && !(fabs(zj) > 2.0 * E);
+          double wk = 0.0;
+          if (small) {
+            for (int c = 0; c < K; ++c) wk = fma(V[c * ZP + lane], V[c * ZP + lane], wk);
+          }
+          double zs = small ? fabs(zj) : INFINITY;
+          double zb = (lane < Z2 && !small) ? fabs(zj) : INFINITY;
+  #pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            wk += __shfl_xor_sync(0xffffffffu, wk, off);
+            zs = fmin(zs, __shfl_xor_sync(0xffffffffu, zs, off));
+            zb = fmin(zb, __shfl_xor_sync(0xffffffffu, zb, off));
+          }
+          const double g = zb - E;
+          const double shift = E * wk + E * E * wk / g;
+          const bool any_small = zs < INFINITY;
+          redo = nonfin || !(E < INFINITY) ||
+                 (any_small && !(g > 0.0 && zs > 2.0 * shift + 64.0 * kEps * zmax));
+        }
       }
       if (redo) {
         // The count is uncertain but the FP32 Newton step is still good: with
@@ -1273,6 +1409,8 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       }
       tau = tn;
       if (conv) {
+        // The null vector comes from Z's eigenpairs at the evaluated point.
+        if (gj) diag_Z();
         // [alpha_0; beta]: eigenvector of Z for the eigenvalue nearest zero.
         int jmin = 0;
         double amin = fabs(Z[0]);
@@ -1359,7 +1497,8 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
   constexpr int KP = K + 1;
   constexpr int Z2 = K + 2;
   constexpr int ZP = K + 3;
-  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
+  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP], sA[G][Z2 * ZP],
+      sI[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
   __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
   __shared__ double s_err[G][2], s_step[G];
@@ -1373,7 +1512,7 @@ __global__ void __launch_bounds__(128) roots_kernel(Sub sub, const int* __restri
     group_sync<E>(g);
     const int m = s_m[g];
     if (m >= stop) break;
-    root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], &s_tau[g],
+    root_solve<K>(sub, pole_cnt, max_iter, out, st, n, m, sM[g], sN[g], sZ[g], sV[g], sA[g], sI[g], &s_tau[g],
                   &s_lamo[g], &s_done[g], &s_ia[g], &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }
@@ -1387,7 +1526,8 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
   constexpr int KP = K + 1;
   constexpr int Z2 = K + 2;
   constexpr int ZP = K + 3;
-  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP];
+  __shared__ double sM[G][K * KP], sN[G][K * KP], sZ[G][Z2 * ZP], sV[G][Z2 * ZP], sA[G][Z2 * ZP],
+      sI[G][Z2 * ZP];
   __shared__ double s_tau[G], s_lamo[G];
   __shared__ int s_m[G], s_done[G], s_ia[G], s_ib[G], s_ph[G], s_tay[G];
   __shared__ double s_err[G][2], s_step[G];
@@ -1407,7 +1547,7 @@ __global__ void __launch_bounds__(128) roots_grouped_kernel(const ProbDesc* __re
     if (input_invalid(d.st)) continue;  // uniform across the group
     const Sub sub = sub_of(d);
     root_solve<K>(sub, d.pole_cnt, max_iter, rootout_of(d), d.st, *sub.n_dev, item - c.pk[p],
-                  sM[g], sN[g], sZ[g], sV[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
+                  sM[g], sN[g], sZ[g], sV[g], sA[g], sI[g], &s_tau[g], &s_lamo[g], &s_done[g], &s_ia[g],
                   &s_ib[g], &s_ph[g], s_err[g], &s_tay[g], &s_step[g], g, e, lane);
   }
 }

@@ -49,6 +49,8 @@ def test_static_scratch_matches_allocating_entry_point():
             assert np.all(np.isfinite(mu))
             assert np.max(np.abs(mu - mu_ref)) <= MU_TOL * scale
             assert np.array_equal(it, it_ref)
+            ref = oracle.update(P["Q"], P["lam"], P["K"], P["sigma"], want_vectors=False)
+            assert np.max(np.abs(mu - ref["mu"])) <= MU_TOL * scale
         n = eu.EIG_STATIC_MAX_N + 1
         big = dev_vec(np.arange(n, dtype=np.float64))
         Ub = dev_colmajor(np.zeros((n, 1)))
