@@ -366,10 +366,11 @@ __device__ void warp_jacobi(double* A, double* V, int lane, bool init_v = true) 
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
-    // Converged when the off-diagonal part is 1e-16 of the diagonal (Frobenius):
-    // it then moves no eigenvalue by more than that (Weyl), below the
-    // rotations' own rounding.
-    if (off == 0.0 || off <= 1e-32 * dia) break;
+    // Converged when the off-diagonal part is 1e-18 of the diagonal (Frobenius).
+    // The eigenvalues would be settled at 1e-16 already; the margin is for the
+    // eigenvectors of the small eigenvalues (the null vector of Z), which an
+    // off-diagonal residual F moves by F / (eigenvalue gap).
+    if (off == 0.0 || off <= 1e-36 * dia) break;
     for (int rnd = 0; rnd < M - 1; ++rnd) {
       int pj = 0, qj = 0;
       double cj = 1.0, sj = 0.0;
@@ -567,11 +568,11 @@ __device__ void warp_jacobi_f32(float* A, float* V, int lane) {
 // Inverse of an N x N matrix Z (row stride N+1, shared memory, left intact) by
 // Gauss-Jordan elimination with partial pivoting, one warp: A is the working
 // copy, B receives Z^{-1}.  Lane c owns column c of A and of B (N <= 32);
-// each row's elimination factor is broadcast from the lane that read it, so
-// no factor is overwritten before use.  Returns false (B invalid)
-// if a pivot is zero or not finite.  *detneg = 1 when det Z < 0 (pivot signs
-// and row swaps); *zf = |Z|_F, *bf = |Z^{-1}|_F, *bkf = |(Z^{-1})_{KK}|_F (the
-// leading KB x KB block).
+// each step first copies the rows' elimination factors (column j) into the
+// spare column N of the row stride, so no factor is overwritten before use.
+// Returns false (B invalid) if a pivot is zero or not finite.  *detneg = 1
+// when det Z < 0 (pivot signs and row swaps); *zf = |Z|_F, *bf = |Z^{-1}|_F,
+// *bkf = |(Z^{-1})_{KK}|_F (the leading KB x KB block).
 // ----------------------------------------------------------------------------
 template <int N>
 __device__ bool warp_gj_inverse(const double* Z, double* A, double* B, int lane, int KB, int* detneg,
@@ -616,19 +617,21 @@ __device__ bool warp_gj_inverse(const double* Z, double* A, double* B, int lane,
     const double pv = A[j * P + j];
     if (pv < 0.0) neg ^= 1;
     const double rp = 1.0 / pv;
-    const double f = (lane < N) ? A[lane * P + j] : 0.0;  // factor of row `lane`
+    // Row factors (column j) go to the spare column N before any row changes.
+    if (lane < N) A[lane * P + N] = A[lane * P + j];
     __syncwarp();
     if (lane < N) {
       A[j * P + lane] *= rp;
       B[j * P + lane] *= rp;
     }
     __syncwarp();
-    const double aj0 = (lane < N) ? A[j * P + lane] : 0.0;
-    const double bj0 = (lane < N) ? B[j * P + lane] : 0.0;
-#pragma unroll 2
-    for (int r = 0; r < N; ++r) {
-      const double fr = __shfl_sync(0xffffffffu, f, r);
-      if (r != j && lane < N) {
+    if (lane < N) {
+      const double aj0 = A[j * P + lane];
+      const double bj0 = B[j * P + lane];
+#pragma unroll 4
+      for (int r = 0; r < N; ++r) {
+        if (r == j) continue;
+        const double fr = A[r * P + N];
         A[r * P + lane] = fma(-fr, aj0, A[r * P + lane]);
         B[r * P + lane] = fma(-fr, bj0, B[r * P + lane]);
       }
