@@ -372,28 +372,41 @@ def run_batched(eu, dev, mode, steps, seed=3000, count=512, oracle_sample=64):
                  want=eu.EIG_VALUES | eu.EIG_VECTORS)
         devs.append(d)
         lam0.append(d["lam"].clone())
-    h = eu.eig_update_init(dev.index or 0, mode)
     stream = torch.cuda.current_stream()
 
-    def step():
-        for d, l0 in zip(devs, lam0):
-            d["lam"].copy_(l0)
-        tk = eu.eig_update_batch(h, devs, stream=stream)
-        return tk
+    def timed(flags):
+        """Rate of `steps` batches on a handle with these init flags (the tuner,
+        if on, times its candidate schedules during the warm-up batches)."""
+        h = eu.eig_update_init(dev.index or 0, mode, flags=flags)
+        tks = []
 
-    for _ in range(2):
-        tk = step()
-    torch.cuda.synchronize()
-    bad = [t for t in tk if eu.eig_update_query(h, eu.EIG_Q_STATUS, t) != 0]
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    eu.eig_update_destroy(h)
+        def step():
+            for d, l0 in zip(devs, lam0):
+                d["lam"].copy_(l0)
+            tk = eu.eig_update_batch(h, devs, stream=stream)
+            tks.append(tk)
+            return tk
+
+        for _ in range(2):
+            tk = step()
+        torch.cuda.synchronize()
+        bad = [t for t in tk if eu.eig_update_query(h, eu.EIG_Q_STATUS, t) != 0]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        met = eu.eig_update_query(h, eu.EIG_Q_METRICS)
+        for tk in tks:
+            for t in tk:
+                eu.eig_update_release(h, t)
+        eu.eig_update_destroy(h)
+        return e0.elapsed_time(e1), bad, met
+
+    ms_untuned, _, _ = timed(0)
+    ms, bad, met = timed(eu.EIG_TUNE)
     pairs = sum(P["lam"].shape[0] for P in probs)
     # Per-instance error against the oracle on a sample of the instances (every
     # root of each sampled update, and the residual of its returned vectors).
@@ -420,9 +433,13 @@ def run_batched(eu, dev, mode, steps, seed=3000, count=512, oracle_sample=64):
     return {"value": pairs * steps / (ms / 1000.0), "unit": UNIT, "updates_per_step": count,
             "eigenpairs_per_step": pairs, "ms_per_step": ms / steps, "steps": steps,
             "failed_updates": len(bad), "input_generation_s": gen_s, "vs_oracle": check,
+            "tuned_vs_untuned": ms_untuned / ms, "untuned_value": pairs * steps / (ms_untuned / 1000.0),
+            "tuner": {"trials": met["tune_trials"], "hits": met["tune_hits"],
+                      "how": "EIG_TUNE: candidate schedules timed on the first batch, the fastest reused"},
             "max_err_vs_oracle": check["max_dmu_rel"] if check else None,
             "workload": "512 updates, n log-uniform [128,2048], k uniform 1..8, lam ~ U[-1,1], "
-                        "Q Haar, K ~ N(0,1)/sqrt(n); one eig_update_batch per step (grouped launches)"}
+                        "Q Haar, K ~ N(0,1)/sqrt(n); one eig_update_batch per step (grouped launches, "
+                        "tuned schedule)"}
 
 
 def run_serving(eu, dev, mode, residents=48, nmin=1024, nmax=8192, chain=100, loads=(0.5, 0.8, 1.0),

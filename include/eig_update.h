@@ -75,8 +75,23 @@ typedef struct {
   uint32_t mode;       /* EIG_FP64 or EIG_MIXED */
   uint64_t hbm_budget; /* max bytes of workspace the handle may hold; 0 = no limit */
   int32_t max_iter;    /* per-root iteration cap of the zero finder; 0 = 128 */
-  uint32_t flags;      /* reserved, must be 0 */
+  uint32_t flags;      /* 0 or EIG_TUNE */
 } eig_init_params;
+
+/* eig_init_params.flags: tune the launch schedule of eig_update_batch.  The
+   first batch of each signature (mode, vectors or not, and per padded rank
+   the number of updates and their total size, in powers of two) times the
+   candidate schedules -- rank classes in sequence or overlapped on one stream
+   each, multi-root pole intervals first or natural root order, the zero
+   finder's persistent grid at full or half residency -- on a values-only copy
+   of the batch (the caller's data is not touched; a few extra passes of the
+   secular stages), keeps the fastest, and reuses it for later batches of that
+   signature.  Results are identical under every schedule.  With the
+   environment variable EIG_TUNE_CACHE naming a file, the choices are read
+   from it at eig_update_init and appended to it as they are made, so a later
+   process starts tuned.  eig_update_rank_k and the serving engine keep the
+   default schedule. */
+#define EIG_TUNE 1u
 
 typedef struct {
   int64_t n;           /* size, >= 1 */
@@ -227,6 +242,8 @@ typedef struct {
   int64_t launches;         /* kernels launched by the update paths */
   int64_t workspace_allocs; /* workspace (re)allocations */
   uint64_t workspace_bytes; /* current workspace size */
+  int64_t tune_trials;      /* EIG_TUNE: schedules timed by the batch tuner */
+  int64_t tune_hits;        /* EIG_TUNE: batch tables that reused a tuned schedule */
 } eig_metrics;
 
 typedef struct {

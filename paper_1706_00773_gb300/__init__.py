@@ -25,7 +25,7 @@ __all__ = [
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
     "eig_server_poll", "eig_server_query", "eig_server_pending", "Server", "eig_location_rank2",
-    "eig_perturbation", "eig_update_select", "eig_pole_counts", "eig_fp64_fma_rate",
+    "eig_perturbation", "eig_update_select", "eig_pole_counts", "eig_fp64_fma_rate", "EIG_TUNE",
 ]
 
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV = 0, -1, -2, -3
@@ -34,6 +34,7 @@ EIG_STATIC_MAX_N = 8192
 EIG_MAX_K = 16
 EIG_FP64, EIG_MIXED = 0, 1
 EIG_VALUES, EIG_VECTORS, EIG_REPORT, EIG_ASYNC = 1, 2, 4, 8
+EIG_TUNE = 1
 EIG_Q_STATUS, EIG_Q_REPORT, EIG_Q_LAST_STATUS, EIG_Q_COUNT, EIG_Q_WORKSPACE, EIG_Q_METRICS = 1, 2, 3, 4, 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,7 +67,8 @@ class eig_metrics(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("updates", ctypes.c_int64), ("eigenpairs", ctypes.c_int64),
                 ("updates_ok", ctypes.c_int64), ("updates_failed", ctypes.c_int64),
                 ("updates_pending", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("workspace_allocs", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_allocs", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
+                ("tune_trials", ctypes.c_int64), ("tune_hits", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -218,8 +220,9 @@ def eig_version() -> str:
     return lib().eig_version().decode()
 
 
-def eig_update_init(device: int = 0, mode: int = EIG_FP64, hbm_budget: int = 0, max_iter: int = 0):
-    p = eig_init_params(device, mode, hbm_budget, max_iter, 0)
+def eig_update_init(device: int = 0, mode: int = EIG_FP64, hbm_budget: int = 0, max_iter: int = 0,
+                    flags: int = 0):
+    p = eig_init_params(device, mode, hbm_budget, max_iter, flags)
     h = ctypes.c_void_p()
     _check(lib().eig_update_init(ctypes.byref(p), ctypes.byref(h)), "eig_update_init")
     return h

@@ -7,8 +7,12 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <new>
 #include <vector>
@@ -169,6 +173,18 @@ struct eig_ctx {
   std::vector<int> free_tickets;
   std::vector<BatchRes> batches;
   std::vector<int> free_batches;
+  // Class-concurrent schedule: one stream per rank class, fork/join events.
+  static constexpr int kAux = 12;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t aux_fork = nullptr;
+  cudaEvent_t aux_join[kAux] = {};
+  bool aux_ready = false;
+  // Batch schedule tuner (EIG_TUNE): best schedule per batch signature,
+  // optionally persisted in the file named by EIG_TUNE_CACHE.
+  bool tune = false;
+  std::map<std::string, Sched> tuned;
+  std::string tune_file;
+  int64_t m_tune_trials = 0, m_tune_hits = 0;
 };
 
 namespace {
@@ -192,6 +208,47 @@ int ensure_ws(eig_ctx* h, size_t bytes) {
   h->ws_bytes = bytes;
   ++h->m_allocs;
   return EIG_OK;
+}
+
+// Streams and events of the class-concurrent schedule (created on first use).
+bool ensure_aux(eig_ctx* h) {
+  if (h->aux_ready) return true;
+  for (int i = 0; i < eig_ctx::kAux; ++i) {
+    if (!h->aux[i] && cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking) != cudaSuccess) break;
+    if (!h->aux_join[i] && cudaEventCreateWithFlags(&h->aux_join[i], cudaEventDisableTiming) != cudaSuccess) break;
+    if (i == eig_ctx::kAux - 1) h->aux_ready = true;
+  }
+  if (h->aux_ready && !h->aux_fork && cudaEventCreateWithFlags(&h->aux_fork, cudaEventDisableTiming) != cudaSuccess)
+    h->aux_ready = false;
+  if (!h->aux_ready) cudaGetLastError();
+  return h->aux_ready;
+}
+
+// The tuner's cache file: one line per batch signature, "key streams order occ_div".
+void load_tune_cache(eig_ctx* h) {
+  const char* f = std::getenv("EIG_TUNE_CACHE");
+  if (!f || !*f) return;
+  h->tune_file = f;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  char key[512];
+  int a = 0, b = 0, c = 0;
+  while (std::fscanf(fp, "%511s %d %d %d", key, &a, &b, &c) == 4) {
+    Sched sc;
+    sc.streams = a < 1 ? 1 : (a > eig_ctx::kAux ? eig_ctx::kAux : a);
+    sc.order = b ? 1 : 0;
+    sc.occ_div = c < 1 ? 1 : (c > 4 ? 4 : c);
+    h->tuned[key] = sc;
+  }
+  std::fclose(fp);
+}
+
+void save_tune_entry(eig_ctx* h, const std::string& key, const Sched& sc) {
+  if (h->tune_file.empty()) return;
+  FILE* fp = std::fopen(h->tune_file.c_str(), "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d %d %d\n", key.c_str(), sc.streams, sc.order, sc.occ_div);
+  std::fclose(fp);
 }
 
 #define CK(x)                         \
@@ -443,7 +500,7 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
 // stream-ordered.  With ev != nullptr, events 0..8 mark the stage boundaries.
 int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixed, bool report,
                   cudaStream_t s, cudaEvent_t* ev, int* launches, const std::vector<char>& img,
-                  const eig_problem* P0, unsigned long long negmask0) {
+                  const eig_problem* P0, unsigned long long negmask0, const Sched& sch = Sched()) {
   int nl = 0;
 #define MARK(i) \
   if (ev) CK(cudaEventRecord(ev[i], s))
@@ -457,23 +514,55 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   CK(launch_deflate_grouped(T.d_desc, count, s));
   ++nl;
   MARK(2);
-  for (size_t c = 0; c < T.classes.size(); ++c) {
-    CK(launch_class_prefix(T.d_desc, T.classes[c], s));
-    CK(launch_counts_grouped(T.d_desc, T.classes[c], T.class_items[c], mixed, s));
-    nl += mixed ? 3 : 2;
-  }
-  MARK(3);
-  for (size_t c = 0; c < T.classes.size(); ++c) {
-    CK(launch_order_roots_grouped(T.d_desc, T.classes[c], T.class_items[c], s));
-    CK(launch_roots_grouped(T.d_desc, T.classes[c], T.class_items[c], h->max_iter, h->num_sms, s));
-    nl += 2;
-  }
-  MARK(4);
-  if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
-  if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
-  for (size_t c = 0; c < T.classes.size(); ++c) {
-    CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));
-    nl += 3;
+  const int ncls = (int)T.classes.size();
+  auto class_of = [&](int c) {
+    ClassDesc cd = T.classes[c];
+    if (!sch.order) cd.perm = nullptr;  // natural root order
+    return cd;
+  };
+  if (sch.streams > 1 && ncls > 1 && h->aux_ready) {
+    // Rank classes overlap: each runs its pole counts, zero finder and
+    // assembly on its own stream (the classes touch disjoint updates), so the
+    // tail of one class's persistent zero finder is filled by the others.
+    if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
+    if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
+    CK(cudaEventRecord(h->aux_fork, s));
+    const int S = std::min(sch.streams, (int)eig_ctx::kAux);
+    for (int c = 0; c < ncls; ++c) {
+      cudaStream_t sc = h->aux[c % S];
+      const ClassDesc cd = class_of(c);
+      CK(cudaStreamWaitEvent(sc, h->aux_fork, 0));
+      CK(launch_class_prefix(T.d_desc, cd, sc));
+      CK(launch_counts_grouped(T.d_desc, cd, T.class_items[c], mixed, sc));
+      CK(launch_order_roots_grouped(T.d_desc, cd, T.class_items[c], sc));
+      CK(launch_roots_grouped(T.d_desc, cd, T.class_items[c], h->max_iter, h->num_sms, sc, sch.occ_div));
+      CK(launch_assemble_grouped(T.d_desc, cd, T.class_items[c], T.class_items[c], vectors, mixed, sc));
+      nl += (mixed ? 3 : 2) + (cd.perm ? 2 : 1) + 3;
+      CK(cudaEventRecord(h->aux_join[c], sc));
+    }
+    for (int c = 0; c < ncls; ++c) CK(cudaStreamWaitEvent(s, h->aux_join[c], 0));
+    MARK(3);
+    MARK(4);
+  } else {
+    for (int c = 0; c < ncls; ++c) {
+      CK(launch_class_prefix(T.d_desc, T.classes[c], s));
+      CK(launch_counts_grouped(T.d_desc, T.classes[c], T.class_items[c], mixed, s));
+      nl += mixed ? 3 : 2;
+    }
+    MARK(3);
+    for (int c = 0; c < ncls; ++c) {
+      const ClassDesc cd = class_of(c);
+      CK(launch_order_roots_grouped(T.d_desc, cd, T.class_items[c], s));
+      CK(launch_roots_grouped(T.d_desc, cd, T.class_items[c], h->max_iter, h->num_sms, s, sch.occ_div));
+      nl += cd.perm ? 2 : 1;
+    }
+    MARK(4);
+    if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
+    if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
+    for (int c = 0; c < ncls; ++c) {
+      CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));
+      nl += 3;
+    }
   }
   if (vectors && T.any_errors) {
     CK(launch_errors_gap_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
@@ -521,6 +610,94 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   MARK(8);
 #undef MARK
   if (launches) *launches = nl;
+  return EIG_OK;
+}
+
+// Batch signature for the tuner: mode, vectors, and per padded rank the
+// number of updates and the size of their secular problems (log2 buckets).
+std::string batch_signature(const std::vector<TableItem>& items, bool vectors, bool mixed) {
+  int cnt[17] = {0};
+  long long tot[17] = {0};
+  for (const TableItem& it : items) {
+    const int K = padded_rank(it.P->k);
+    ++cnt[K];
+    tot[K] += it.P->n;
+  }
+  auto lg = [](long long v) {
+    int b = 0;
+    while (v > 1) {
+      v >>= 1;
+      ++b;
+    }
+    return b;
+  };
+  std::string key = std::string(mixed ? "m" : "d") + (vectors ? "v" : "e");
+  for (int K = 1; K <= 16; ++K)
+    if (cnt[K]) key += "|" + std::to_string(K) + ":" + std::to_string(lg(cnt[K])) + ":" + std::to_string(lg(tot[K]));
+  return key;
+}
+
+// Times the candidate schedules on a values-only copy of the table (each
+// problem's lambda redirected to a workspace copy: the caller's data is not
+// touched) and returns the fastest.  Every schedule gives identical results.
+int tune_table(eig_ctx* h, const std::vector<TableItem>& items, bool mixed, cudaStream_t s, Sched* best) {
+  const int count = (int)items.size();
+  std::vector<eig_problem> tp(count);
+  std::vector<TableItem> ti(count);
+  size_t lam_bytes = 0;
+  std::vector<size_t> lam_off(count);
+  for (int i = 0; i < count; ++i) {
+    tp[i] = *items[i].P;
+    tp[i].want = EIG_VALUES;
+    tp[i].Q_out = nullptr;
+    tp[i].errors = nullptr;
+    ti[i] = items[i];
+    ti[i].P = &tp[i];
+    ti[i].report = false;
+    lam_off[i] = lam_bytes;
+    lam_bytes += align_up(sizeof(double) * (size_t)tp[i].n, 256);
+  }
+  const size_t need = lam_bytes + layout_table(h, ti, nullptr, false, mixed, nullptr).bytes;
+  int rc = ensure_ws(h, need);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) tp[i].lambda = reinterpret_cast<double*>(h->ws + lam_off[i]);
+  std::vector<char> img;
+  Table T = layout_table(h, ti, h->ws + lam_bytes, false, mixed, &img);
+  if (T.bytes == 0) return EIG_ECUDA;
+  const int S = std::min((int)T.classes.size(), (int)eig_ctx::kAux);
+  std::vector<Sched> cand;
+  std::vector<int> stream_opts{1};
+  if (S > 1) stream_opts.push_back(S);
+  for (int st : stream_opts)
+    for (int od : {1, 2})
+      for (int ord : {1, 0}) {
+        Sched c;
+        c.streams = st;
+        c.order = ord;
+        c.occ_div = od;
+        cand.push_back(c);
+      }
+  float best_ms = -1.f;
+  for (int t = -1; t < (int)cand.size(); ++t) {  // t = -1: warm-up
+    const Sched& c = cand[t < 0 ? 0 : t];
+    for (int i = 0; i < count; ++i)
+      CK(cudaMemcpyAsync(tp[i].lambda, items[i].P->lambda, sizeof(double) * (size_t)tp[i].n,
+                         cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(h->ev[0], s));
+    int nl = 0;
+    rc = enqueue_table(h, T, count, false, mixed, false, s, nullptr, &nl, img, nullptr, 0, c);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->ev[1], s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    if (t < 0) continue;
+    ++h->m_tune_trials;
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      *best = c;
+    }
+  }
   return EIG_OK;
 }
 
@@ -577,7 +754,7 @@ int eig_update_init(const eig_init_params* params, eig_handle* out) {
   *out = nullptr;
   eig_init_params p{};
   if (params) p = *params;
-  if (p.flags != 0 || (p.mode != EIG_FP64 && p.mode != EIG_MIXED) || p.max_iter < 0)
+  if ((p.flags & ~EIG_TUNE) != 0 || (p.mode != EIG_FP64 && p.mode != EIG_MIXED) || p.max_iter < 0)
     return EIG_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || p.device < 0 || p.device >= ndev) {
@@ -590,6 +767,8 @@ int eig_update_init(const eig_init_params* params, eig_handle* out) {
   h->mode = p.mode;
   h->budget = p.hbm_budget;
   h->max_iter = p.max_iter ? p.max_iter : kDefaultMaxIter;
+  h->tune = (p.flags & EIG_TUNE) != 0;
+  if (h->tune) load_tune_cache(h);
   DeviceGuard g(h->device);
   if (!g.ok || cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
       cudaMallocHost(&h->st_host, sizeof(DevStatus)) != cudaSuccess ||
@@ -617,6 +796,11 @@ int eig_update_destroy(eig_handle h) {
       if (b.host) cudaFreeHost(b.host);
     }
     if (h->ws) cudaFree(h->ws);
+    for (auto& a : h->aux)
+      if (a) cudaStreamDestroy(a);
+    for (auto& e : h->aux_join)
+      if (e) cudaEventDestroy(e);
+    if (h->aux_fork) cudaEventDestroy(h->aux_fork);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->chk_host) cudaFreeHost(h->chk_host);
     for (auto& e : h->ev)
@@ -748,6 +932,27 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
     tab[v].push_back({&probs[i], negmask, kplus, false});
     slot[v].push_back(i);
   }
+  // Schedule of each table: the tuned one for its signature (EIG_TUNE; timed
+  // now if the signature is new), else the default sequential schedule.
+  Sched sch[2];
+  if (h->tune && (tab[0].size() + tab[1].size()) > 1 && ensure_aux(h)) {
+    for (int v = 0; v < 2; ++v) {
+      if (tab[v].empty()) continue;
+      const std::string key = batch_signature(tab[v], v == 1, mixed);
+      auto it = h->tuned.find(key);
+      if (it != h->tuned.end()) {
+        sch[v] = it->second;
+        ++h->m_tune_hits;
+        continue;
+      }
+      Sched best;
+      const int trc = tune_table(h, tab[v], mixed, s, &best);
+      if (trc) return trc;
+      h->tuned[key] = best;
+      save_tune_entry(h, key, best);
+      sch[v] = best;
+    }
+  }
   size_t need = 0;
   for (int v = 0; v < 2; ++v)
     if (!tab[v].empty()) need = std::max(need, layout_table(h, tab[v], nullptr, v == 1, mixed, nullptr).bytes);
@@ -779,7 +984,7 @@ int eig_update_batch(eig_handle h, int32_t count, eig_problem* probs, uint64_t* 
     Table T = layout_table(h, tab[v], h->ws, v == 1, mixed, &img);
     if (T.bytes == 0) return fail(EIG_ECUDA);
     int nl = 0;
-    rc = enqueue_table(h, T, (int)tab[v].size(), v == 1, mixed, false, s, nullptr, &nl, img, nullptr, 0);
+    rc = enqueue_table(h, T, (int)tab[v].size(), v == 1, mixed, false, s, nullptr, &nl, img, nullptr, 0, sch[v]);
     if (rc) return fail(rc);
     {
       std::lock_guard<std::mutex> lk(h->mu);
@@ -938,6 +1143,8 @@ int eig_update_query(eig_handle h, int32_t what, const void* in, void* out, size
       m.launches = h->m_launches;
       m.workspace_allocs = h->m_allocs;
       m.workspace_bytes = h->ws_bytes;
+      m.tune_trials = h->m_tune_trials;
+      m.tune_hits = h->m_tune_hits;
       for (const Ticket& t : h->tickets) {  // live batch tickets: resolved now, without waiting
         if (!t.live) continue;
         const int status = ticket_status(h, t, nullptr);

@@ -279,6 +279,14 @@ struct ClassDesc {
   int* perm;      // class items in the order the zero finder takes them (null: natural order)
 };
 
+// Launch schedule of a table's secular stages (results are identical for
+// every schedule: it orders and overlaps work, it does not change arithmetic).
+struct Sched {
+  int streams = 1;  // > 1: each rank class's stages on its own stream (classes overlap)
+  int order = 1;    // 1: roots of multi-root pole intervals first; 0: natural order
+  int occ_div = 1;  // zero-finder persistent grid at 1/occ_div of the resident blocks
+};
+
 // ---- launch wrappers (defined in the .cu files) ----------------------------
 cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* K, double* U,
                                cudaStream_t s);
@@ -307,8 +315,10 @@ cudaError_t launch_class_prefix(const ProbDesc* P, const ClassDesc& c, cudaStrea
 // of those; FP64 mode ignores passes.
 cudaError_t launch_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, bool mixed,
                                   cudaStream_t s, int passes = 3);
+// occ_div > 1 caps the persistent grid at 1/occ_div of the resident blocks
+// per SM (a schedule choice of the batch tuner; results are unchanged).
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
-                                 int num_sms, cudaStream_t s);
+                                 int num_sms, cudaStream_t s, int occ_div = 1);
 // Order the zero finder's work: roots in pole intervals that hold several roots
 // (the ones that need the most evaluations) first, so they do not finish last.
 cudaError_t launch_order_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, cudaStream_t s);

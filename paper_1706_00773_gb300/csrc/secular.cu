@@ -91,9 +91,9 @@ cudaError_t launch_order_roots_grouped(const ProbDesc* P, const ClassDesc& c, in
 }
 
 cudaError_t launch_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
-                                 int num_sms, cudaStream_t s) {
+                                 int num_sms, cudaStream_t s, int occ_div) {
   switch (c.K) {
-#define R_(K_) case K_: return sec_roots_grouped<K_>(P, c, max_items, max_iter, num_sms, s);
+#define R_(K_) case K_: return sec_roots_grouped<K_>(P, c, max_items, max_iter, num_sms, s, occ_div);
     R_(1) R_(2) R_(3) R_(4) R_(5) R_(6) R_(7) R_(8) R_(10) R_(12) R_(14) R_(16)
 #undef R_
     default: return cudaErrorInvalidValue;

@@ -26,7 +26,7 @@ cudaError_t sec_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_it
                                cudaStream_t s);
 template <int K>
 cudaError_t sec_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter, int num_sms,
-                              cudaStream_t s);
+                              cudaStream_t s, int occ_div);
 template <int K>
 cudaError_t sec_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_defl,
                                  bool vectors, bool mixed, cudaStream_t s);

@@ -2135,7 +2135,7 @@ cudaError_t counts_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_item
 
 template <int K>
 cudaError_t roots_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter,
-                            int num_sms, cudaStream_t s) {
+                            int num_sms, cudaStream_t s, int occ_div) {
   constexpr int G = 4 / warps_per_root(K);
   if (g_occ_roots_grouped[K] == 0) {
     int occ = 0;
@@ -2145,7 +2145,8 @@ cudaError_t roots_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_items
     g_occ_roots_grouped[K] = occ > 0 ? occ : 1;
   }
   long long want = ((long long)max_items + G - 1) / G;
-  long long cap = (long long)num_sms * g_occ_roots_grouped[K];
+  const int per_sm = g_occ_roots_grouped[K] / (occ_div > 1 ? occ_div : 1);
+  long long cap = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
   roots_grouped_kernel<K><<<blocks, 128, 0, s>>>(P, c, max_iter);
@@ -2198,8 +2199,8 @@ cudaError_t sec_counts_grouped(const ProbDesc* P, const ClassDesc& c, int max_it
 }
 template <int K>
 cudaError_t sec_roots_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_iter, int num_sms,
-                              cudaStream_t s) {
-  return roots_grouped_k<K>(P, c, max_items, max_iter, num_sms, s);
+                              cudaStream_t s, int occ_div) {
+  return roots_grouped_k<K>(P, c, max_items, max_iter, num_sms, s, occ_div);
 }
 template <int K>
 cudaError_t sec_assemble_grouped(const ProbDesc* P, const ClassDesc& c, int max_items, int max_defl,

@@ -21,7 +21,7 @@ template cudaError_t sec_assemble_select<EIG_SECULAR_K>(const Sub&, const RootOu
 template cudaError_t sec_counts_grouped<EIG_SECULAR_K>(const ProbDesc*, const ClassDesc&, int, bool, int,
                                                        cudaStream_t);
 template cudaError_t sec_roots_grouped<EIG_SECULAR_K>(const ProbDesc*, const ClassDesc&, int, int, int,
-                                                      cudaStream_t);
+                                                      cudaStream_t, int);
 template cudaError_t sec_assemble_grouped<EIG_SECULAR_K>(const ProbDesc*, const ClassDesc&, int, int, bool, bool,
                                                          cudaStream_t);
 
