@@ -179,6 +179,10 @@ struct eig_ctx {
   cudaEvent_t aux_fork = nullptr;
   cudaEvent_t aux_join[kAux] = {};
   bool aux_ready = false;
+  // Side stream: the BF16 slicing of Q (mixed mode) overlaps the secular stages.
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  bool side_ready = false;
   // Batch schedule tuner (EIG_TUNE): best schedule per batch signature,
   // optionally persisted in the file named by EIG_TUNE_CACHE.
   bool tune = false;
@@ -222,6 +226,17 @@ bool ensure_aux(eig_ctx* h) {
     h->aux_ready = false;
   if (!h->aux_ready) cudaGetLastError();
   return h->aux_ready;
+}
+
+bool ensure_side(eig_ctx* h) {
+  if (h->side_ready) return true;
+  if ((h->side || cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess) &&
+      (h->side_fork || cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) == cudaSuccess) &&
+      (h->side_join || cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) == cudaSuccess))
+    h->side_ready = true;
+  else
+    cudaGetLastError();
+  return h->side_ready;
 }
 
 // The tuner's cache file: one line per batch signature, "key streams order occ_div".
@@ -424,6 +439,7 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     d.taur = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
     d.runs = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
     d.errors = vectors ? P->errors : nullptr;
+    d.Pp = reinterpret_cast<double*>(b.take(sizeof(double) * ld * (size_t)(K * (K + 1) / 2)));
     if (d.errors) T.any_errors = true;
     if (n > T.max_n) T.max_n = n;
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
@@ -512,8 +528,23 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   nl += 2;
   MARK(1);
   CK(launch_deflate_grouped(T.d_desc, count, s));
-  ++nl;
+  CK(launch_products_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
+  nl += 2;
   MARK(2);
+  // Mixed mode: Q's BF16 digit slices depend on Q (and the rotation of runs
+  // of equal lambda) only, so they are formed on the side stream while the
+  // secular stages run (HBM-bound work next to FP64-bound work); the GEMM
+  // waits for them.
+  const bool side = vectors && mixed && sch.side && ensure_side(h);
+  if (side) {
+    CK(cudaEventRecord(h->side_fork, s));
+    CK(cudaStreamWaitEvent(h->side, h->side_fork, 0));
+    CK(launch_runs_rotate_q_grouped(T.d_desc, count, h->num_sms, h->side));
+    CK(cudaMemsetAsync(T.d_rmax, 0, T.rmax_bytes, h->side));
+    CK(launch_slice_q_grouped(T.d_desc, count, T.d_rbpre, T.total_rb, T.d_slpre, T.total_sl, h->side));
+    nl += 4;
+    CK(cudaEventRecord(h->side_join, h->side));
+  }
   const int ncls = (int)T.classes.size();
   auto class_of = [&](int c) {
     ClassDesc cd = T.classes[c];
@@ -571,10 +602,14 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   MARK(5);
   if (vectors) {
     if (mixed) {
-      CK(launch_runs_rotate_q_grouped(T.d_desc, count, h->num_sms, s));
-      CK(cudaMemsetAsync(T.d_rmax, 0, T.rmax_bytes, s));
-      CK(launch_slice_q_grouped(T.d_desc, count, T.d_rbpre, T.total_rb, T.d_slpre, T.total_sl, s));
-      nl += 4;
+      if (side) {
+        CK(cudaStreamWaitEvent(s, h->side_join, 0));
+      } else {
+        CK(launch_runs_rotate_q_grouped(T.d_desc, count, h->num_sms, s));
+        CK(cudaMemsetAsync(T.d_rmax, 0, T.rmax_bytes, s));
+        CK(launch_slice_q_grouped(T.d_desc, count, T.d_rbpre, T.total_rb, T.d_slpre, T.total_sl, s));
+        nl += 4;
+      }
       MARK(6);
       CK(launch_gemm_tc_grouped(T.d_desc, count, T.d_maps, T.d_gtpre, T.total_gt, s));
       ++nl;
@@ -801,6 +836,9 @@ int eig_update_destroy(eig_handle h) {
     for (auto& e : h->aux_join)
       if (e) cudaEventDestroy(e);
     if (h->aux_fork) cudaEventDestroy(h->aux_fork);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->side_fork) cudaEventDestroy(h->side_fork);
+    if (h->side_join) cudaEventDestroy(h->side_join);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->chk_host) cudaFreeHost(h->chk_host);
     for (auto& e : h->ev)
@@ -1395,7 +1433,8 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   const size_t qs_bytes = tc ? align_up(2 * (size_t)tc_num_slices() * tc_slice_plane((int)n), 256) : 0;
   const size_t ws_bytes = tc ? align_up(2 * (size_t)tc_num_slices() * (size_t)tc_slice_ld((int)n) * capc, 256) : 0;
   const size_t aux_bytes = tc ? align_up(8 * (size_t)n, 256) + align_up(4 * (size_t)n, 256) + align_up(4 * capc, 256) : 0;
-  const size_t need = base + 256 + f32_bytes + wsel_bytes + qs_bytes + ws_bytes + aux_bytes;
+  const size_t pp_bytes = align_up(sizeof(double) * (size_t)ld * (size_t)(Kp * (Kp + 1) / 2), 256);
+  const size_t need = base + 256 + f32_bytes + wsel_bytes + qs_bytes + ws_bytes + aux_bytes + pp_bytes;
   int rc = ensure_ws(h, need);
   if (rc) return rc;
   Carve c = plan(h->ws, n, k, false, false, false);
@@ -1412,6 +1451,8 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   int* fcol = tc ? reinterpret_cast<int*>(tcb + qs_bytes + ws_bytes + align_up(8 * (size_t)n, 256) +
                                           align_up(4 * (size_t)n, 256))
                  : nullptr;
+  // products of the kept rows, as the update's zero finder takes them
+  double* Pp = reinterpret_cast<double*>(tcb + qs_bytes + ws_bytes + aux_bytes);
   const double xv[2] = {vl, vu};
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
@@ -1431,6 +1472,8 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   sub.negmask = negmask;
   sub.lamf = lamf;
   sub.Usf = Usf;
+  CK(launch_products(c.Us, Kp, ld, c.st, Pp, s));
+  sub.Pp = Pp;
   CK(launch_counts(sub, pts, 2, win + 8, s));
   CK(launch_select_window(sub, c.st, c.lam_defl, vl, vu, win + 8, win, s));
   int hw[8];
@@ -1637,8 +1680,10 @@ int srv_launch(eig_srv* S, SrvSlot& sl) {
   Table T = layout_table(S->h, items, sl.ws + koff, true, S->mixed, &img);
   if (T.bytes == 0) return EIG_ECUDA;
   int nl = 0;
+  Sched sch;
+  sch.side = false;  // the slots share the handle: keep each batch on its slot's stream
   int rc = enqueue_table(S->h, T, (int)items.size(), true, S->mixed, false, sl.stream, nullptr, &nl, img,
-                         nullptr, 0);
+                         nullptr, 0, sch);
   if (rc) return rc;
   CK(cudaMemcpyAsync(sl.st_host, T.d_st, sizeof(DevStatus) * items.size(), cudaMemcpyDeviceToHost,
                      sl.stream));

@@ -193,7 +193,58 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_grouped_kernel(const Pro
                d.lam_defl, d.st, d.lam_old, d.lamf, d.Usf);
 }
 
+// u_ia u_ib for every kept row i and a <= b (the upper triangle row by row),
+// written as K(K+1)/2 arrays of ld doubles; one thread per row.
+__global__ void products_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                        const long long* __restrict__ colpre) {
+  const long long total = colpre[count];
+  for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+       item += (long long)gridDim.x * blockDim.x) {
+    const int q = find_owner(colpre, count, item);
+    const ProbDesc& d = P[q];
+    if (!d.Pp || (d.st->flags & (ST_UNSORTED | ST_NONFINITE))) continue;
+    const int i = (int)(item - colpre[q]);
+    if (i >= d.st->n_keep) continue;
+    const int K = d.K, ld = d.ld;
+    int s = 0;
+    for (int a = 0; a < K; ++a) {
+      const double ua = d.Us[(size_t)a * ld + i];
+      for (int b = a; b < K; ++b, ++s) d.Pp[(size_t)s * ld + i] = ua * d.Us[(size_t)b * ld + i];
+    }
+  }
+}
+
+__global__ void products_kernel(const double* __restrict__ Us, int K, int ld, const DevStatus* st,
+                                double* __restrict__ Pp) {
+  if (st->flags & (ST_UNSORTED | ST_NONFINITE)) return;
+  const int nk = st->n_keep;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
+    int s = 0;
+    for (int a = 0; a < K; ++a) {
+      const double ua = Us[(size_t)a * ld + i];
+      for (int b = a; b < K; ++b, ++s) Pp[(size_t)s * ld + i] = ua * Us[(size_t)b * ld + i];
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_products(const double* Us, int K, int ld, const DevStatus* st, double* Pp, cudaStream_t s) {
+  int blocks = (ld + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  products_kernel<<<blocks, 256, 0, s>>>(Us, K, ld, st, Pp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_products_grouped(const ProbDesc* P, int count, const long long* colpre, long long total,
+                                    cudaStream_t s) {
+  long long blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  products_grouped_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, count, colpre);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s) {
   deflate_grouped_kernel<<<count, kDeflThreads, 0, s>>>(P);

@@ -100,6 +100,11 @@ struct Sub {
   // lam' as (hi, lo) float pairs, U' as K float arrays of ld.
   const float2* lamf = nullptr;
   const float* Usf = nullptr;
+  // Products u_ia u_ib (a <= b, row-major over the upper triangle) of every
+  // kept row, K(K+1)/2 arrays of ld doubles (null: form them from Us).  The
+  // zero finder's FP64 sums then take M^_ab += r_i (u_ia u_ib) without the K
+  // multiplications t = r u per term.
+  const double* Pp = nullptr;
 };
 
 // Per-root outputs of the zero finder.
@@ -224,6 +229,7 @@ struct ProbDesc {
   double* taur;            // their scalars (n)
   int* runs;               // (g0, m) pairs (n ints)
   double* errors;          // caller: n x 4 per-eigenpair report (column-major), or null
+  double* Pp;              // products u_ia u_ib of the kept rows, K(K+1)/2 arrays of ld (see Sub)
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
@@ -239,6 +245,7 @@ __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
   s.negmask = d.negmask;
   s.lamf = d.lamf;
   s.Usf = d.Usf;
+  s.Pp = d.Pp;
   return s;
 }
 
@@ -285,6 +292,7 @@ struct Sched {
   int streams = 1;  // > 1: each rank class's stages on its own stream (classes overlap)
   int order = 1;    // 1: roots of multi-root pole intervals first; 0: natural order
   int occ_div = 1;  // zero-finder persistent grid at 1/occ_div of the resident blocks
+  bool side = true; // mixed mode: Q's slices on a side stream, overlapping the secular stages
 };
 
 // ---- launch wrappers (defined in the .cu files) ----------------------------
@@ -296,6 +304,12 @@ cudaError_t launch_project_grouped(const ProbDesc* P, int count, const long long
                                    long long total_cols, cudaStream_t s);
 // Deflation + compaction for every update (one CTA each); also keeps lam_old.
 cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s);
+// Products u_ia u_ib of the kept rows into ProbDesc::Pp (updates with Pp set);
+// colpre: device prefix of n over the table.
+cudaError_t launch_products_grouped(const ProbDesc* P, int count, const long long* colpre, long long total,
+                                    cudaStream_t s);
+// The same for one sub-problem (Us: K arrays of ld; n' read from st).
+cudaError_t launch_products(const double* Us, int K, int ld, const DevStatus* st, double* Pp, cudaStream_t s);
 // Runs of exactly repeated lam (runs.cu): QR of each run's rows of U before
 // deflation, then B applied to W's rows (FP64 GEMM paths) or Q~ = Q B written
 // to Xout (split-BF16 path).

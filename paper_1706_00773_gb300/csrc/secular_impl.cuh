@@ -221,6 +221,91 @@ __device__ __forceinline__ int accumulate_group(int e, const double* __restrict_
                                                  skip_b, sA, sB, lane, Usf);
 }
 
+// The zero finder's FP64 sums from the products p_i,ab = u_ia u_ib of the
+// kept rows (Sub::Pp): M^_ab += r_i p_i,ab, one FMA per entry and no t = r u
+// multiplications.  N^ as in accumulate: FP64 N^_ab += r_i^2 p_i,ab (ACC_MN) or
+// FP32 from the FP32 copy of U' (ACC_MN32).  Same terms in the same order per
+// lane as accumulate; the products themselves are rounded once, so M^ differs
+// from accumulate's by rounding only.
+template <int K, int E, int e, int MODE>
+__device__ __forceinline__ void accumulate_p(const double* __restrict__ lam, const double* __restrict__ Pp,
+                                             int ld, int n, double lam_o, double tau, int skip_a, int skip_b,
+                                             double* sA, double* sB, int lane, const float* __restrict__ Usf) {
+  static_assert(MODE == ACC_MN || MODE == ACC_MN32, "zero-finder sums only");
+  constexpr int NS = nslots<K, E, e>();
+  constexpr int KP = K + 1;
+  using BT = typename pick_type<MODE == ACC_MN32, float, double>::type;
+  double A[NS];
+  BT B[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = 0.0;
+    B[s] = (BT)0;
+  }
+  for (int i = lane; i < n; i += 32) {
+    const double d = tau - (__ldg(lam + i) - lam_o);
+    const double r = (i == skip_a || i == skip_b) ? 0.0 : rcp_nr(d);
+    float tf[K];
+    if (MODE == ACC_MN32) {
+      const float rf = (float)r;
+#pragma unroll
+      for (int c = 0; c < K; ++c) tf[c] = __ldg(Usf + (size_t)c * ld + i) * rf;
+    }
+    const double r2 = (MODE == ACC_MN) ? r * r : 0.0;
+    int s = 0, g = 0;  // s: this warp's slot, g: slot of the full upper triangle
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+      for (int b = a; b < K; ++b, ++g) {
+        if (owner_of<K, E>(a) == e) {
+          const double pv = __ldg(Pp + (size_t)g * ld + i);
+          A[s] = fma(r, pv, A[s]);
+          if (MODE == ACC_MN) B[s] = (BT)fma(r2, pv, (double)B[s]);
+          if (MODE == ACC_MN32) B[s] = (BT)fmaf(tf[a], tf[b], (float)B[s]);
+          ++s;
+        }
+      }
+    }
+  }
+  double B64[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    A[s] = warp_sum(A[s]);
+    B64[s] = (MODE == ACC_MN32) ? (double)warp_sum_f((float)B[s]) : warp_sum((double)B[s]);
+  }
+  if (lane == 0) {
+    int s = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (owner_of<K, E>(a) == e) {
+#pragma unroll
+        for (int b = a; b < K; ++b) {
+          sA[a * KP + b] = A[s];
+          sA[b * KP + a] = A[s];
+          sB[a * KP + b] = B64[s];
+          sB[b * KP + a] = B64[s];
+          ++s;
+        }
+      }
+    }
+  }
+}
+
+template <int K, int E, int MODE>
+__device__ __forceinline__ void accumulate_p_group(int e, const double* __restrict__ lam,
+                                                   const double* __restrict__ Pp, int ld, int n, double lam_o,
+                                                   double tau, int skip_a, int skip_b, double* sA, double* sB,
+                                                   int lane, const float* __restrict__ Usf) {
+  if (E == 1 || e == 0)
+    accumulate_p<K, E, 0, MODE>(lam, Pp, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, Usf);
+  else if (E > 1 && e == 1)
+    accumulate_p<K, E, (E > 1 ? 1 : 0), MODE>(lam, Pp, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, Usf);
+  else if (E > 2 && e == 2)
+    accumulate_p<K, E, (E > 2 ? 2 : 0), MODE>(lam, Pp, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, Usf);
+  else
+    accumulate_p<K, E, (E > 3 ? 3 : 0), MODE>(lam, Pp, ld, n, lam_o, tau, skip_a, skip_b, sA, sB, lane, Usf);
+}
+
 // ----------------------------------------------------------------------------
 // FP32 accumulation for the coarse phase of the zero finder (mixed mode).
 // The same sums as ACC_MN with x - lam_i formed from (hi, lo) float pairs as
@@ -1052,6 +1137,13 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       const float ho = (float)lam_o, th32 = (float)tau_c;
       accumulate32_group<K, E, true>(e, sub.lamf, sub.Usf, ld, n, ho, (float)(lam_o - (double)ho), th32,
                                (float)(tau_c - (double)th32), skip_a, skip_b, sMg, sNg, s_err, lane);
+    } else if (sub.Pp) {
+      if (sub.Usf)
+        accumulate_p_group<K, E, ACC_MN32>(e, lam, sub.Pp, ld, n, lam_o, tau_c, skip_a, skip_b, sMg, sNg, lane,
+                                           sub.Usf);
+      else
+        accumulate_p_group<K, E, ACC_MN>(e, lam, sub.Pp, ld, n, lam_o, tau_c, skip_a, skip_b, sMg, sNg, lane,
+                                         nullptr);
     } else if (sub.Usf) {
       accumulate_group<K, E, ACC_MN32>(e, lam, Us, ld, n, lam_o, false, tau_c, skip_a, skip_b, sMg, sNg,
                                        lane, sub.Usf);
