@@ -439,7 +439,11 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     d.taur = reinterpret_cast<double*>(b.take(sizeof(double) * ld));
     d.runs = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
     d.errors = vectors ? P->errors : nullptr;
-    d.Pp = reinterpret_cast<double*>(b.take(sizeof(double) * ld * (size_t)(K * (K + 1) / 2)));
+    // Products for the one-warp ranks only: with K >= 10 each warp multiplies
+    // just its own rows (t = r u for a quarter of them), and the product loads
+    // cost more than they save (measured k = 16: 83 -> 86 ms).
+    d.Pp = warps_per_root(K) == 1 ? reinterpret_cast<double*>(b.take(sizeof(double) * ld * (size_t)(K * (K + 1) / 2)))
+                                  : nullptr;
     if (d.errors) T.any_errors = true;
     if (n > T.max_n) T.max_n = n;
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
@@ -1472,8 +1476,10 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   sub.negmask = negmask;
   sub.lamf = lamf;
   sub.Usf = Usf;
-  CK(launch_products(c.Us, Kp, ld, c.st, Pp, s));
-  sub.Pp = Pp;
+  if (warps_per_root(Kp) == 1) {  // as the update: products for the one-warp ranks
+    CK(launch_products(c.Us, Kp, ld, c.st, Pp, s));
+    sub.Pp = Pp;
+  }
   CK(launch_counts(sub, pts, 2, win + 8, s));
   CK(launch_select_window(sub, c.st, c.lam_defl, vl, vu, win + 8, win, s));
   int hw[8];
