@@ -316,6 +316,8 @@ struct Table {
   size_t Ws_bytes = 0;
   unsigned long long* d_rmax = nullptr;
   size_t rmax_bytes = 0;
+  unsigned* d_wnz = nullptr;  // non-zero maps of W's leading slices (mixed mode)
+  size_t wnz_bytes = 0;
   std::vector<ClassDesc> classes;
   std::vector<int> class_items;  // sum of n per class (grid bound)
   long long total_cols = 0, total_copy = 0;
@@ -379,12 +381,13 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
   }
   // --- shared contiguous regions ---
   T.d_st = reinterpret_cast<DevStatus*>(b.take(sizeof(DevStatus) * count));
-  size_t Wtot = 0, Wstot = 0, rtot = 0;
+  size_t Wtot = 0, Wstot = 0, rtot = 0, ztot = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t n = items[i].P->n;
     Wtot += sizeof(double) * (size_t)n * n;
     Wstot += 2 * (size_t)tc_num_slices() * tc_slice_plane((int)n);
     rtot += sizeof(unsigned long long) * (size_t)n;
+    ztot += sizeof(unsigned) * wnz_words((int)n);
   }
   if (vectors && !mixed) {
     T.d_W = reinterpret_cast<double*>(b.take(Wtot));
@@ -395,12 +398,14 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     T.Ws_bytes = Wstot;
     T.d_rmax = reinterpret_cast<unsigned long long*>(b.take(rtot));
     T.rmax_bytes = rtot;
+    T.d_wnz = reinterpret_cast<unsigned*>(b.take(ztot));
+    T.wnz_bytes = ztot;
   }
   // --- per-update regions ---
   std::vector<ProbDesc> desc(count);
   std::vector<long long> colpre(count + 1, 0), cppre(count + 1, 0);
   std::vector<int> rbpre(count + 1, 0), slpre(count + 1, 0), gtpre(count + 1, 0);
-  size_t woff = 0, wsoff = 0, roff = 0;
+  size_t woff = 0, wsoff = 0, roff = 0, woff2 = 0;
   for (int i = 0; i < count; ++i) {
     const eig_problem* P = items[i].P;
     const int64_t n = P->n;
@@ -459,6 +464,8 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
         d.fcol = reinterpret_cast<int*>(b.take(sizeof(int) * ld));
         d.rmax = T.d_rmax ? reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(T.d_rmax) + roff) : nullptr;
         roff += sizeof(unsigned long long) * (size_t)n;
+        d.wnz = T.d_wnz ? reinterpret_cast<unsigned*>(reinterpret_cast<char*>(T.d_wnz) + woff2) : nullptr;
+        woff2 += sizeof(unsigned) * wnz_words((int)n);
       } else {
         d.W = T.d_W ? reinterpret_cast<double*>(reinterpret_cast<char*>(T.d_W) + woff) : nullptr;
         woff += sizeof(double) * (size_t)n * n;
@@ -560,6 +567,7 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
     // assembly on its own stream (the classes touch disjoint updates), so the
     // tail of one class's persistent zero finder is filled by the others.
     if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
+    if (vectors && mixed) CK(cudaMemsetAsync(T.d_wnz, 0, T.wnz_bytes, s));
     if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
     CK(cudaEventRecord(h->aux_fork, s));
     const int S = std::min(sch.streams, (int)eig_ctx::kAux);
@@ -593,6 +601,7 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
     }
     MARK(4);
     if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
+    if (vectors && mixed) CK(cudaMemsetAsync(T.d_wnz, 0, T.wnz_bytes, s));
     if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
     for (int c = 0; c < ncls; ++c) {
       CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));

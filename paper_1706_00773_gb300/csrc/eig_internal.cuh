@@ -186,7 +186,16 @@ struct WSlices {
   size_t plane = 0;
   int lds = 0;
   int* fcol = nullptr;
+  // Non-zero map of the two leading slices (null: not kept): word
+  // (r / 128) * nch + j / 32 gets bit q when slice q (q = 0, 1) has a non-zero
+  // entry in that 128-column x 32-row tile of W^T -- the tiles of the split
+  // GEMM, which skips MMAs against all-zero ones.
+  unsigned* wnz = nullptr;
+  int nch = 0;
 };
+
+// Tiles of the W-slice non-zero map for an n x n update: 128 columns x 32 rows.
+__host__ __device__ inline size_t wnz_words(int n) { return (size_t)((n + 127) / 128) * (size_t)((n + 31) / 32); }
 
 // ---- one update as seen by the grouped kernels -------------------------------
 // Every launch processes a table of updates (a single update is a table of
@@ -230,6 +239,7 @@ struct ProbDesc {
   int* runs;               // (g0, m) pairs (n ints)
   double* errors;          // caller: n x 4 per-eigenpair report (column-major), or null
   double* Pp;              // products u_ia u_ib of the kept rows, K(K+1)/2 arrays of ld (see Sub)
+  unsigned* wnz;           // mixed mode: non-zero map of W's two leading slices (see WSlices)
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {

@@ -166,6 +166,11 @@ struct GemmArgs {
   const DevStatus* st;  // skip on invalid input (may be null)
   int* err;             // timeout flag (status flags word)
   int tiles_m, tiles_n;
+  // Non-zero map of W's slices 0 and 1 per 128-column x 32-row tile (bits 0,
+  // 1; word tn * nch + kb), or null: MMAs against an all-zero W tile are
+  // skipped (their products are exactly zero).
+  const unsigned* wnz = nullptr;
+  int nch = 0;
 };
 
 // One 128 x 128 output tile (the whole CTA takes part).
@@ -258,12 +263,18 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
+      // Exact groups: whether an MMA has reset the group's accumulator in the
+      // current chunk (the first one of a chunk overwrites, the rest add).
+      bool started[3] = {false, false, false};
       for (int kb = 0; kb < nk && ok; ++kb) {
         const int s = kb % kStages;
         const uint32_t ph = (kb / kStages) & 1;
         const int chunk = kb / kStagesPerChunk;
         const bool first_in_chunk = (kb % kStagesPerChunk) == 0;
         const bool last_in_chunk = ((kb % kStagesPerChunk) == kStagesPerChunk - 1) || (kb == nk - 1);
+        // which of W's slices 0 and 1 have non-zeros in this stage's tile
+        const unsigned wbits = a.wnz ? __ldg(a.wnz + (size_t)tn * a.nch + kb) : 3u;
+        if (first_in_chunk) started[0] = started[1] = started[2] = false;
         if (first_in_chunk && chunk > 0) {
           if (!mbar_wait(bar_acce, (chunk - 1) & 1)) {
             ok = false;
@@ -281,12 +292,12 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
         tc_fence_after();
         const uint32_t st_base = sbase + s * kStageBytes;
         // exact groups: g = p + q (0-based) in {0, 1, 2} -> TMEM columns 0, 128, 256
-        bool started[3] = {!first_in_chunk, !first_in_chunk, !first_in_chunk};
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
 #pragma unroll
           for (int p = 0; p <= g; ++p) {
             const int q = g - p;
+            if (q <= 1 && !((wbits >> q) & 1u)) continue;  // all-zero W tile
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
               const uint64_t ad = smem_desc(st_base + p * kTileBytes + ks * 32);
@@ -296,7 +307,20 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
             }
           }
         }
-        if (last_in_chunk) tc_commit(bar_accf);
+        if (last_in_chunk) {
+          // A group that saw no MMA in this chunk still holds the last chunk's
+          // sum: overwrite it with a product against this stage's all-zero W
+          // slice 0 (every pair of the group was skipped, (g, 0) included).
+#pragma unroll
+          for (int g = 0; g < 3; ++g) {
+            if (started[g]) continue;
+            const uint64_t ad = smem_desc(st_base + g * kTileBytes);
+            const uint64_t bd = smem_desc(st_base + kSlices * kTileBytes);
+            tc_mma(tmem + g * BN, ad, bd, 0u);
+            started[g] = true;
+          }
+          tc_commit(bar_accf);
+        }
         // tail groups: p + q in {3, 4} -> TMEM column 384, accumulated over all K
 #pragma unroll
         for (int g = 3; g < kSlices; ++g) {
@@ -304,6 +328,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
           for (int p = 0; p <= g; ++p) {
             const int q = g - p;
             if (p >= kSlices || q >= kSlices) continue;
+            if (q <= 1 && !((wbits >> q) & 1u)) continue;  // all-zero W tile (never the first MMA: q = 3)
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
               const uint64_t ad = smem_desc(st_base + p * kTileBytes + ks * 32);
@@ -421,6 +446,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   a.err = &d.st->flags;
   a.tiles_m = (d.n + BM - 1) / BM;
   a.tiles_n = a.tiles_m;
+  a.wnz = d.wnz;
+  a.nch = (d.n + 31) / 32;
   gemm_tc_tile(mq, mw, a, (int)blockIdx.x - tile_prefix[p]);
 }
 
