@@ -567,7 +567,6 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
     // assembly on its own stream (the classes touch disjoint updates), so the
     // tail of one class's persistent zero finder is filled by the others.
     if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
-    if (vectors && mixed) CK(cudaMemsetAsync(T.d_wnz, 0, T.wnz_bytes, s));
     if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
     CK(cudaEventRecord(h->aux_fork, s));
     const int S = std::min(sch.streams, (int)eig_ctx::kAux);
@@ -601,7 +600,6 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
     }
     MARK(4);
     if (vectors && mixed) CK(cudaMemsetAsync(T.d_Ws, 0, T.Ws_bytes, s));
-    if (vectors && mixed) CK(cudaMemsetAsync(T.d_wnz, 0, T.wnz_bytes, s));
     if (vectors && !mixed) CK(cudaMemsetAsync(T.d_W, 0, T.W_bytes, s));
     for (int c = 0; c < ncls; ++c) {
       CK(launch_assemble_grouped(T.d_desc, T.classes[c], T.class_items[c], T.class_items[c], vectors, mixed, s));
@@ -624,8 +622,9 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
         nl += 4;
       }
       MARK(6);
+      CK(launch_wnz_scan_grouped(T.d_desc, count, T.d_gtpre, T.total_gt, s));
       CK(launch_gemm_tc_grouped(T.d_desc, count, T.d_maps, T.d_gtpre, T.total_gt, s));
-      ++nl;
+      nl += 2;
     } else {
       CK(launch_runs_apply_w_grouped(T.d_desc, count, h->num_sms, s));
       ++nl;

@@ -186,15 +186,12 @@ struct WSlices {
   size_t plane = 0;
   int lds = 0;
   int* fcol = nullptr;
-  // Non-zero map of the two leading slices (null: not kept): word
-  // (r / 128) * nch + j / 32 gets bit q when slice q (q = 0, 1) has a non-zero
-  // entry in that 128-column x 32-row tile of W^T -- the tiles of the split
-  // GEMM, which skips MMAs against all-zero ones.
-  unsigned* wnz = nullptr;
-  int nch = 0;
 };
 
-// Tiles of the W-slice non-zero map for an n x n update: 128 columns x 32 rows.
+// Words of the non-zero map of W's two leading digit slices for an n x n
+// update: word (r / 128) * ceil(n / 32) + j / 32 has bit q set when slice q
+// (q = 0, 1) holds a non-zero entry in that 128-column x 32-row tile of W^T,
+// the operand tiles of the split GEMM, which skips MMAs against all-zero ones.
 __host__ __device__ inline size_t wnz_words(int n) { return (size_t)((n + 127) / 128) * (size_t)((n + 31) / 32); }
 
 // ---- one update as seen by the grouped kernels -------------------------------
@@ -440,6 +437,10 @@ cudaError_t launch_slice_q_grouped(const ProbDesc* P, int count, const int* rb_p
 int tc_encode_map(void* map64, const void* base, int n);  // 0 on success
 cudaError_t launch_gemm_tc_grouped(const ProbDesc* P, int count, const void* maps, const int* tile_prefix,
                                    int total_tiles, cudaStream_t s);
+// The non-zero map (ProbDesc::wnz) of every update's W slices, one CTA per
+// 128 x 128 GEMM tile (tile_prefix as for the GEMM).
+cudaError_t launch_wnz_scan_grouped(const ProbDesc* P, int count, const int* tile_prefix, int total_tiles,
+                                    cudaStream_t s);
 cudaError_t launch_gemm_f64_grouped(const ProbDesc* P, int count, const int* tile_prefix, int total_tiles,
                                     cudaStream_t s);
 // X -> Q copy-back for in-place updates; elem_prefix: prefix of n*n (device).

@@ -451,6 +451,49 @@ __global__ void __launch_bounds__(kThreads, 1)
   gemm_tc_tile(mq, mw, a, (int)blockIdx.x - tile_prefix[p]);
 }
 
+// Non-zero map of W's slices 0 and 1: CTA = one 128 x 128 GEMM tile of an
+// update (128 columns r of W^T, 128 rows j = four 32-row chunks); thread t
+// reads column r = r0 + t % 128 of slice t / 128, 64 bytes per chunk.
+__global__ void __launch_bounds__(256) wnz_scan_grouped_kernel(const ProbDesc* __restrict__ P, int count,
+                                                               const int* __restrict__ tile_prefix) {
+  __shared__ unsigned flags[4];
+  const int p = find_owner(tile_prefix, count, (int)blockIdx.x);
+  const ProbDesc& d = P[p];
+  if (!d.wnz || (d.st->flags & (ST_UNSORTED | ST_NONFINITE))) return;  // uniform across the CTA
+  const int n = d.n;
+  const int tiles = (n + BM - 1) / BM;
+  const int local = (int)blockIdx.x - tile_prefix[p];
+  const int jb = local / tiles, rt = local % tiles;
+  const int nch = (n + 31) / 32;
+  const int lds = (n + 63) / 64 * 64;
+  const size_t plane = (size_t)lds * (size_t)n;
+  if (threadIdx.x < 4) flags[threadIdx.x] = 0u;
+  __syncthreads();
+  const int q = threadIdx.x >> 7;
+  const int r = rt * BN + (threadIdx.x & 127);
+  if (r < n) {
+    const __nv_bfloat16* row = d.Ws + (size_t)q * plane + (size_t)r * lds;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j0 = jb * BM + c * 32;
+      if (j0 >= lds) break;
+      const uint4* v = reinterpret_cast<const uint4*>(row + j0);  // 64 bytes, 16-byte aligned
+      unsigned nz = 0u;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const uint4 x = __ldcg(v + w);
+        nz |= (x.x | x.y | x.z | x.w) & 0x7fff7fffu;  // any non-zero BF16 (either sign of zero ignored)
+      }
+      if (nz) atomicOr(&flags[c], 1u << q);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int ch = jb * 4 + threadIdx.x;
+    if (ch < nch) d.wnz[(size_t)rt * nch + ch] = flags[threadIdx.x];
+  }
+}
+
 // ---- slicing ------------------------------------------------------------------
 // Row maxima of |Q| (column-major), as ordered bit patterns of non-negative doubles.
 __global__ void rowmax_kernel(int n, const double* __restrict__ Q,
@@ -661,6 +704,13 @@ cudaError_t launch_gemm_tc_grouped(const ProbDesc* P, int count, const void* map
   if (e != cudaSuccess) return e;
   gemm_tc_grouped_kernel<<<total_tiles, kThreads, kSmemBytes, s>>>(
       reinterpret_cast<const CUtensorMap*>(maps), P, tile_prefix, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wnz_scan_grouped(const ProbDesc* P, int count, const int* tile_prefix, int total_tiles,
+                                    cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  wnz_scan_grouped_kernel<<<total_tiles, 256, 0, s>>>(P, count, tile_prefix);
   return cudaGetLastError();
 }
 

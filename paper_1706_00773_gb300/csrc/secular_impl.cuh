@@ -1703,23 +1703,6 @@ __global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_
 constexpr int kAsmThreads = 256;
 constexpr int kAsmCache = 32;
 
-// Marks the tiles of W^T that hold non-zero entries of slices 0 and 1 (bits
-// 0, 1) for one entry per lane (bits 0 for lanes with no entry).  The lanes of
-// a warp usually share one tile: then one atomic for the warp.
-__device__ __forceinline__ void mark_wnz(const WSlices& ws, int64_t pos, int j, unsigned bits) {
-  const unsigned any = __ballot_sync(0xffffffffu, bits != 0u);
-  if (!any) return;
-  const size_t key = (size_t)(pos >> 7) * (size_t)ws.nch + (size_t)(j >> 5);
-  const int lead = __ffs(any) - 1;
-  const size_t key0 = (size_t)__shfl_sync(0xffffffffu, (unsigned long long)key, lead);
-  if (__all_sync(0xffffffffu, bits == 0u || key == key0)) {
-    const unsigned b = __reduce_or_sync(0xffffffffu, bits);
-    if ((threadIdx.x & 31) == lead) atomicOr(ws.wnz + key0, b);
-  } else if (bits) {
-    atomicOr(ws.wnz + key, bits);
-  }
-}
-
 // Sum over the CTA of one value per thread (every thread gets the sum); sh
 // holds kAsmThreads / 32 doubles and may be reused right after.
 __device__ __forceinline__ double block_sum_asm(double v, double* sh) {
@@ -1923,32 +1906,21 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
 #pragma unroll
       for (int c = 0; c < kAsmCache; ++c) {
         const int i = t + c * kAsmThreads;
-        unsigned bits = 0u;
-        int j = 0;
         if (i < nk) {
           __nv_bfloat16 d[kTcSlices];
           tc_split_prescaled(wc[c], s2, d);
-          j = sub.idx[i];
+          const int j = sub.idx[i];
 #pragma unroll
           for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
-          bits = (__bfloat16_as_ushort(d[0]) & 0x7fffu ? 1u : 0u) | (__bfloat16_as_ushort(d[1]) & 0x7fffu ? 2u : 0u);
         }
-        if (ws.wnz && c * kAsmThreads < nk) mark_wnz(ws, pos, j, bits);  // warp-uniform condition
       }
     } else {
-      for (int i0 = 0; i0 < nk; i0 += kAsmThreads) {
-        const int i = i0 + t;
-        unsigned bits = 0u;
-        int j = 0;
-        if (i < nk) {
-          __nv_bfloat16 d[kTcSlices];
-          tc_split_prescaled(wcomp(i), s2, d);
-          j = sub.idx[i];
+      for (int i = t; i < nk; i += kAsmThreads) {
+        __nv_bfloat16 d[kTcSlices];
+        tc_split_prescaled(wcomp(i), s2, d);
+        const int j = sub.idx[i];
 #pragma unroll
-          for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
-          bits = (__bfloat16_as_ushort(d[0]) & 0x7fffu ? 1u : 0u) | (__bfloat16_as_ushort(d[1]) & 0x7fffu ? 2u : 0u);
-        }
-        if (ws.wnz) mark_wnz(ws, pos, j, bits);
+        for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
       }
     }
   }
@@ -1991,8 +1963,6 @@ __device__ __forceinline__ WSlices wslices_of(const ProbDesc& d, bool mixed) {
     ws.lds = (d.n + 63) / 64 * 64;
     ws.plane = (size_t)ws.lds * (size_t)d.n;
     ws.fcol = d.fcol;
-    ws.wnz = d.wnz;
-    ws.nch = (d.n + 31) / 32;
   }
   return ws;
 }
@@ -2036,7 +2006,6 @@ __global__ void deflated_grouped_kernel(const ProbDesc* __restrict__ P, ClassDes
       const int lds = (d.n + 63) / 64 * 64;
       d.Ws[(size_t)pos * lds + d.idx_defl[j]] = __double2bfloat16(64.0);
       d.fcol[pos] = 2;
-      if (d.wnz) atomicOr(d.wnz + (size_t)(pos >> 7) * ((d.n + 31) / 32) + (d.idx_defl[j] >> 5), 1u);
     }
     if (vectors && d.errors) {
       // w = e_i: r = U Sigma u_i, |r| <= |U|_F |u_i| (the deflation bound),
