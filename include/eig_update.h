@@ -439,6 +439,15 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
  * if the device cannot be used. */
 int eig_fp64_fma_rate(int32_t device, int32_t reps, double* gflops, void* stream);
 
+/* ---- diagnostics -----------------------------------------------------------
+ * The CUDA runtime error behind the calling thread's most recent EIG_ECUDA
+ * from a checked stream-ordered call (0 if there was none; later successful
+ * calls do not clear it).  When msg is not NULL and len > 0, writes at most
+ * len bytes, NUL-terminated: the error's name and description and the call
+ * that returned it ("" if none).  Returns the cudaError_t value.  Never
+ * touches the device. */
+int eig_last_cuda_error(char* msg, int32_t len);
+
 /* Library version string (static storage). */
 const char* eig_version(void);
 

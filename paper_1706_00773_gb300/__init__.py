@@ -21,7 +21,7 @@ __all__ = [
     "EIG_REPORT", "EIG_ASYNC", "EIG_MAX_K", "EIG_Q_STATUS", "EIG_Q_REPORT", "EIG_Q_LAST_STATUS",
     "EIG_Q_COUNT", "EIG_Q_WORKSPACE", "EIG_Q_METRICS", "EigError", "lib", "library_path", "colmajor",
     "eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch", "eig_update_release",
-    "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version",
+    "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2", "eig_version", "eig_last_cuda_error",
     "eig_count", "Updater", "eig_secular_values_static", "EIG_ETOOBIG", "EIG_STATIC_MAX_N",
     "eig_server_create", "eig_server_destroy", "eig_server_add_resident", "eig_server_submit",
     "eig_server_poll", "eig_server_query", "eig_server_pending", "Server", "eig_location_rank2",
@@ -46,9 +46,11 @@ _NAMES = {EIG_OK: "EIG_OK", EIG_EINVAL: "EIG_EINVAL", EIG_ENOMEM: "EIG_ENOMEM",
 
 
 class EigError(RuntimeError):
-    def __init__(self, code: int, what: str):
-        super().__init__("%s failed: %s (%d)" % (what, _NAMES.get(code, "?"), code))
+    def __init__(self, code: int, what: str, detail: str = ""):
+        super().__init__("%s failed: %s (%d)%s" % (what, _NAMES.get(code, "?"), code,
+                                                   (": " + detail) if detail else ""))
         self.code = code
+        self.detail = detail
 
 
 class eig_init_params(ctypes.Structure):
@@ -151,6 +153,8 @@ def lib() -> ctypes.CDLL:
                   "eig_server_poll", "eig_server_query", "eig_server_pending"):
             getattr(L, f).restype = ctypes.c_int
         L.eig_version.restype = ctypes.c_char_p
+        L.eig_last_cuda_error.argtypes = [ctypes.c_char_p, i32]
+        L.eig_last_cuda_error.restype = ctypes.c_int
         for f in ("eig_update_init", "eig_update_destroy", "eig_update_rank_k", "eig_update_batch",
                   "eig_update_release", "eig_update_query", "eig_project", "eig_secular_values", "eig_make_rank2",
                   "eig_secular_values_static", "eig_location_rank2", "eig_perturbation",
@@ -207,9 +211,20 @@ def _sigma_buf(sigma, k):
     return buf, ctypes.cast(buf, ctypes.c_void_p)
 
 
+def eig_last_cuda_error():
+    """(code, message) of the CUDA error behind this thread's last EIG_ECUDA (0, "" if none)."""
+    buf = ctypes.create_string_buffer(256)
+    code = lib().eig_last_cuda_error(buf, 256)
+    return code, buf.value.decode(errors="replace")
+
+
 def _check(rc: int, what: str, ok=(EIG_OK,)):
     if rc not in ok:
-        raise EigError(rc, what)
+        detail = ""
+        if rc == EIG_ECUDA:
+            code, msg = eig_last_cuda_error()
+            detail = msg if code else ""
+        raise EigError(rc, what, detail)
     return rc
 
 

@@ -266,13 +266,23 @@ void save_tune_entry(eig_ctx* h, const std::string& key, const Sched& sc) {
   std::fclose(fp);
 }
 
-#define CK(x)                         \
-  do {                                \
-    cudaError_t e_ = (x);             \
-    if (e_ != cudaSuccess) {          \
-      cudaGetLastError();             \
-      return EIG_ECUDA;               \
-    }                                 \
+// The CUDA call behind the calling thread's last EIG_ECUDA (eig_last_cuda_error).
+thread_local int t_cuda_err = 0;
+thread_local char t_cuda_call[192] = {0};
+
+void note_cuda(cudaError_t e, const char* call, int line) {
+  t_cuda_err = (int)e;
+  std::snprintf(t_cuda_call, sizeof(t_cuda_call), "api.cu:%d %s", line, call);
+}
+
+#define CK(x)                             \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) {              \
+      note_cuda(e_, #x, __LINE__);        \
+      cudaGetLastError();                 \
+      return EIG_ECUDA;                   \
+    }                                     \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -796,6 +806,18 @@ extern "C" {
 
 const char* eig_version(void) { return "eigupdate-gb300 0.1 (sm_103a)"; }
 
+int eig_last_cuda_error(char* msg, int32_t len) {
+  if (msg && len > 0) {
+    if (t_cuda_err == 0) {
+      msg[0] = '\0';
+    } else {
+      std::snprintf(msg, (size_t)len, "%s: %s (%s)", cudaGetErrorName((cudaError_t)t_cuda_err),
+                    cudaGetErrorString((cudaError_t)t_cuda_err), t_cuda_call);
+    }
+  }
+  return t_cuda_err;
+}
+
 int eig_update_init(const eig_init_params* params, eig_handle* out) {
   if (!out) return EIG_EINVAL;
   *out = nullptr;
@@ -804,7 +826,9 @@ int eig_update_init(const eig_init_params* params, eig_handle* out) {
   if ((p.flags & ~EIG_TUNE) != 0 || (p.mode != EIG_FP64 && p.mode != EIG_MIXED) || p.max_iter < 0)
     return EIG_EINVAL;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p.device < 0 || p.device >= ndev) {
+  const cudaError_t de = cudaGetDeviceCount(&ndev);
+  if (de != cudaSuccess || p.device < 0 || p.device >= ndev) {
+    note_cuda(de != cudaSuccess ? de : cudaErrorInvalidDevice, "cudaGetDeviceCount", __LINE__);
     cudaGetLastError();
     return EIG_ECUDA;
   }

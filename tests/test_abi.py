@@ -69,6 +69,10 @@ def test_init_without_gpu_fails_cleanly(built_lib):
     with pytest.raises(eu.EigError) as ei:
         eu.eig_update_init(0)
     assert ei.value.code == eu.EIG_ECUDA
+    # the failing runtime call is recorded for the thread and carried by the error
+    code, msg = eu.eig_last_cuda_error()
+    assert code != 0 and "cudaGetDeviceCount" in msg, (code, msg)
+    assert "cudaGetDeviceCount" in ei.value.detail
 
 
 def test_struct_layouts_match_header(tmp_path):
