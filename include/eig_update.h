@@ -160,6 +160,13 @@ typedef struct {
   double max_pair_residual; /* with eig_problem.errors: max of its columns 0, */
   double max_pair_rayleigh; /* 1 and 3 over every eigenpair (0 without) */
   double max_pair_orth;
+  int64_t tc_pair_tiles;    /* EIG_MIXED full update with vectors: 128 x 128 x 32
+                               BF16 slice-pair products the tcgen05 GEMM issued
+                               (2 * 128 * 128 * 32 flops each): 15 per output
+                               tile and 32-deep step, less the pairs against
+                               all-zero tiles of W's two leading slices, which
+                               it skips (their products are exactly zero).
+                               0 where that GEMM did not run. */
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

@@ -776,6 +776,7 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->max_pair_residual = st.err_max[0];
   rep->max_pair_rayleigh = st.err_max[1];
   rep->max_pair_orth = st.err_max[2];
+  rep->tc_pair_tiles = st.tc_pair_tiles;
   if (chk) {
     const int nc = (int)(P->n < kCheckCols ? P->n : kCheckCols);
     double r = 0.0, o = 0.0;

@@ -52,6 +52,7 @@ struct DevStatus {
   int run_rows;            // rows in those runs
   double err_max[3];       // per-eigenpair report maxima: residual, Rayleigh shift,
                            // next-vector dot (non-negative: atomicMax on the bits)
+  long long tc_pair_tiles; // 128 x 128 x 32 BF16 slice-pair products the split GEMM issues
 };
 
 // Public status of a finished update from its device status block (shared by

@@ -121,6 +121,34 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
+// Three 16-column loads (one per exact group, columns `col` of each) and one
+// wait: the waits, not the loads, dominate the drain.  The outputs are
+// early-clobber: a later load's address must not share a register with an
+// earlier load's destination.
+__device__ __forceinline__ void tc_ld16x3(uint32_t t0, uint32_t t1, uint32_t t2, float (&v)[3][16]) {
+  uint32_t r[48];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+      "%27, %28, %29, %30, %31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, "
+      "%43, %44, %45, %46, %47}, [%50];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=&r"(r[0]), "=&r"(r[1]), "=&r"(r[2]), "=&r"(r[3]), "=&r"(r[4]), "=&r"(r[5]), "=&r"(r[6]), "=&r"(r[7]),
+        "=&r"(r[8]), "=&r"(r[9]), "=&r"(r[10]), "=&r"(r[11]), "=&r"(r[12]), "=&r"(r[13]), "=&r"(r[14]),
+        "=&r"(r[15]), "=&r"(r[16]), "=&r"(r[17]), "=&r"(r[18]), "=&r"(r[19]), "=&r"(r[20]), "=&r"(r[21]),
+        "=&r"(r[22]), "=&r"(r[23]), "=&r"(r[24]), "=&r"(r[25]), "=&r"(r[26]), "=&r"(r[27]), "=&r"(r[28]),
+        "=&r"(r[29]), "=&r"(r[30]), "=&r"(r[31]), "=&r"(r[32]), "=&r"(r[33]), "=&r"(r[34]), "=&r"(r[35]),
+        "=&r"(r[36]), "=&r"(r[37]), "=&r"(r[38]), "=&r"(r[39]), "=&r"(r[40]), "=&r"(r[41]), "=&r"(r[42]),
+        "=&r"(r[43]), "=&r"(r[44]), "=&r"(r[45]), "=&r"(r[46]), "=&r"(r[47])
+      : "r"(t0), "r"(t1), "r"(t2)
+      : "memory");
+#pragma unroll
+  for (int g = 0; g < 3; ++g)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[g][i] = __uint_as_float(r[16 * g + i]);
+}
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -135,13 +163,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: K-major operand tile, 64-byte swizzle,
-// 8-row core groups 512 bytes apart (SBO), version 1, layout SWIZZLE_64B (4).
+// Shared-memory matrix descriptor: K-major operand tile of 64-byte rows (32
+// BF16, two MMA K steps), 64-byte swizzle, 8-row core groups 512 bytes apart
+// (SBO), version 1, layout SWIZZLE_64B (4).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
   d |= (uint64_t)1 << 16;                          // leading byte offset (unused, swizzled)
-  d |= (uint64_t)((512 >> 4) & 0x3FFFu) << 32;     // stride byte offset
+  d |= (uint64_t)((8 * BK * 2 >> 4) & 0x3FFFu) << 32;  // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                          // descriptor version
   d |= (uint64_t)4 << 61;                          // SWIZZLE_64B
   return d;
@@ -167,7 +196,7 @@ struct GemmArgs {
   int* err;             // timeout flag (status flags word)
   int tiles_m, tiles_n;
   // Non-zero map of W's slices 0 and 1 per 128-column x 32-row tile (bits 0,
-  // 1; word tn * nch + kb), or null: MMAs against an all-zero W tile are
+  // 1; word tn * nch + j / 32), or null: MMAs against an all-zero W tile are
   // skipped (their products are exactly zero).
   const unsigned* wnz = nullptr;
   int nch = 0;
@@ -273,7 +302,7 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
         const bool first_in_chunk = (kb % kStagesPerChunk) == 0;
         const bool last_in_chunk = ((kb % kStagesPerChunk) == kStagesPerChunk - 1) || (kb == nk - 1);
         // which of W's slices 0 and 1 have non-zeros in this stage's tile
-        const unsigned wbits = a.wnz ? __ldg(a.wnz + (size_t)tn * a.nch + kb) : 3u;
+        const unsigned wbits = a.wnz ? __ldg(a.wnz + (size_t)tn * a.nch + (kb * BK) / 32) : 3u;
         if (first_in_chunk) started[0] = started[1] = started[2] = false;
         if (first_in_chunk && chunk > 0) {
           if (!mbar_wait(bar_acce, (chunk - 1) & 1)) {
@@ -367,14 +396,13 @@ __device__ __forceinline__ void gemm_tc_tile(const CUtensorMap* mapQp, const CUt
       tc_fence_after();
 #pragma unroll
       for (int cb = 0; cb < 4; ++cb) {
-        const uint32_t col = (uint32_t)(half * 64 + cb * 16);
+        const uint32_t col = tmem + lane_addr + (uint32_t)(half * 64 + cb * 16);
+        float v[3][16];
+        tc_ld16x3(col, col + BN, col + 2 * BN, v);
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {
-          float v[16];
-          tc_ld16(tmem + lane_addr + g * BN + col, v);
+        for (int g = 0; g < 3; ++g)
 #pragma unroll
-          for (int c = 0; c < 16; ++c) df_add(hi[cb * 16 + c], lo[cb * 16 + c], v[c]);
-        }
+          for (int c = 0; c < 16; ++c) df_add(hi[cb * 16 + c], lo[cb * 16 + c], v[g][c]);
       }
       tc_fence_before();
       __syncwarp();
@@ -488,9 +516,23 @@ __global__ void __launch_bounds__(256) wnz_scan_grouped_kernel(const ProbDesc* _
     }
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
-    const int ch = jb * 4 + threadIdx.x;
-    if (ch < nch) d.wnz[(size_t)rt * nch + ch] = flags[threadIdx.x];
+  if (threadIdx.x < 32) {
+    // Slice-pair products the GEMM issues for these K steps of tile column rt,
+    // over every tile row: 15 per step, less the 5 pairs (p, 0) when slice 0
+    // is all zero and the 4 pairs (p, 1) when slice 1 is.
+    unsigned long long issued = 0ull;
+    if (threadIdx.x < 4) {
+      const int ch = jb * 4 + threadIdx.x;
+      if (ch < nch) {
+        const unsigned f = flags[threadIdx.x];
+        d.wnz[(size_t)rt * nch + ch] = f;
+        issued = (unsigned long long)(15 - ((f & 1u) ? 0 : 5) - ((f & 2u) ? 0 : 4)) * (unsigned long long)tiles;
+      }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) issued += __shfl_down_sync(0xffffffffu, issued, o);
+    if (threadIdx.x == 0 && issued)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&d.st->tc_pair_tiles), issued);
   }
 }
 

@@ -293,6 +293,41 @@ def test_mixed_matches_fp64_and_oracle(eu, handle, handle_mixed, n, k, sigma):
     assert rep["max_orth"] <= 1e-10
 
 
+def _pair_products_full(n):
+    t = (n + 127) // 128
+    return 15 * t * t * ((n + 31) // 32)
+
+
+def test_mixed_gemm_pair_products_issued(eu, handle, handle_mixed):
+    """report.tc_pair_tiles: the split GEMM issues 15 slice-pair products per
+    128 x 128 output tile and 32-deep step, less 5 where W's slice 0 is all zero
+    in that tile and 4 where slice 1 is; 0 where the split GEMM does not run."""
+    # W = I (every pole deflates): slice 0 holds one entry per column (the
+    # unit), slice 1 none.  In tile column tn only the step holding a column's
+    # diagonal has slice 0 non-zero: 11 pairs there, 6 in every other step.
+    n = 1000
+    P = workloads.general(n, 3, seed=11)
+    P["K"] = np.zeros_like(P["K"])
+    rc, rep, mu, X = _run_update(eu, handle_mixed, P)
+    assert rc == 0 and rep["n_deflated"] == n
+    assert np.array_equal(mu, P["lam"])
+    assert np.max(np.abs(X - P["Q"])) <= 1e-11  # Q through its 5 BF16 slices
+    t, nch = (n + 127) // 128, (n + 31) // 32
+    assert rep["tc_pair_tiles"] == t * (6 * t * nch + 5 * nch)
+    # a secular update: between the 6 pairs never skipped (q >= 2) and all 15
+    P = workloads.general(2100, 8, seed=3008, sigma="mixed", lam_kind="logspec")
+    rc, rep, mu, X = _run_update(eu, handle_mixed, P)
+    assert rc == 0
+    full = _pair_products_full(2100)
+    assert 6 * full // 15 <= rep["tc_pair_tiles"] <= full
+    _check_full(P, mu, X)
+    # no split GEMM: FP64 mode, eigenvalues only
+    rc, rep, _, _ = _run_update(eu, handle, P)
+    assert rc == 0 and rep["tc_pair_tiles"] == 0
+    rc, rep, _, _ = _run_update(eu, handle_mixed, P, want=eu.EIG_VALUES | eu.EIG_REPORT)
+    assert rc == 0 and rep["tc_pair_tiles"] == 0
+
+
 def test_mixed_full_size_sampled(eu, handle_mixed):
     P = workloads.general_rank_k(k=8, seed=2000, n=8192, device="cuda:0")
     rc, rep, mu, X = _run_update(eu, handle_mixed, P)
