@@ -167,6 +167,13 @@ typedef struct {
                                all-zero tiles of W's two leading slices, which
                                it skips (their products are exactly zero).
                                0 where that GEMM did not run. */
+  int64_t asm_fp64_cols;    /* EIG_MIXED with vectors: columns of W whose eq. (10)
+                               entries were formed in FP64 instead of the
+                               double-float path: those asking for
+                               eig_problem.errors, those of a sub-problem above
+                               8192 rows, and those whose values leave the
+                               double-float range (magnitudes outside
+                               [2^-60, 2^60]).  0 otherwise. */
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

@@ -464,6 +464,7 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
       d.lamf = reinterpret_cast<float2*>(b.take(sizeof(float2) * ld));
       d.Usf = reinterpret_cast<float*>(b.take(sizeof(float) * ld * K));
+      d.Ulo = vectors ? reinterpret_cast<float*>(b.take(sizeof(float) * ld * K)) : nullptr;
     }
     if (vectors) {
       if (mixed) {
@@ -777,6 +778,7 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->max_pair_rayleigh = st.err_max[1];
   rep->max_pair_orth = st.err_max[2];
   rep->tc_pair_tiles = st.tc_pair_tiles;
+  rep->asm_fp64_cols = st.asm_fp64_cols;
   if (chk) {
     const int nc = (int)(P->n < kCheckCols ? P->n : kCheckCols);
     double r = 0.0, o = 0.0;

@@ -77,7 +77,7 @@ __device__ __forceinline__ void deflate_body(
     unsigned long long negmask, double* __restrict__ lam_keep, double* __restrict__ Us, int ld,
     int* __restrict__ idx_keep, int* __restrict__ idx_defl, double* __restrict__ lam_defl,
     DevStatus* st, double* __restrict__ lam_old, float2* __restrict__ lamf = nullptr,
-    float* __restrict__ Usf = nullptr) {
+    float* __restrict__ Usf = nullptr, float* __restrict__ Ulo = nullptr) {
   __shared__ double shd[kDeflThreads];
   __shared__ int shi[kDeflThreads];
   __shared__ double colsq[EIG_MAX_K];
@@ -140,7 +140,12 @@ __device__ __forceinline__ void deflate_body(
         // lam = hi + lo + O(2^-48 |lam|): the FP32 phase forms lam_i - lam_o from the pairs
         const float hi = (float)lam[i];
         lamf[pk] = make_float2(hi, (float)(lam[i] - (double)hi));
-        for (int c = 0; c < k; ++c) Usf[(int64_t)c * ld + pk] = (float)U[(int64_t)c * n + i];
+        for (int c = 0; c < k; ++c) {
+          const double u = U[(int64_t)c * n + i];
+          const float uh = (float)u;
+          Usf[(int64_t)c * ld + pk] = uh;
+          if (Ulo) Ulo[(int64_t)c * ld + pk] = (float)(u - (double)uh);
+        }
       }
       ++pk;
     } else {
@@ -155,6 +160,7 @@ __device__ __forceinline__ void deflate_body(
     for (int64_t i = from + t; i < ld; i += kDeflThreads) {
       Us[(int64_t)c * ld + i] = 0.0;
       if (Usf) Usf[(int64_t)c * ld + i] = 0.0f;
+      if (Ulo) Ulo[(int64_t)c * ld + i] = 0.0f;
     }
   }
   __syncthreads();
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kDeflThreads) deflate_kernel(
 __global__ void __launch_bounds__(kDeflThreads) deflate_grouped_kernel(const ProbDesc* __restrict__ P) {
   const ProbDesc& d = P[blockIdx.x];
   deflate_body(d.n, d.k, d.K, d.lam, d.U, d.negmask, d.lam_keep, d.Us, d.ld, d.idx_keep, d.idx_defl,
-               d.lam_defl, d.st, d.lam_old, d.lamf, d.Usf);
+               d.lam_defl, d.st, d.lam_old, d.lamf, d.Usf, d.Ulo);
 }
 
 // u_ia u_ib for every kept row i and a <= b (the upper triangle row by row),

@@ -53,6 +53,7 @@ struct DevStatus {
   double err_max[3];       // per-eigenpair report maxima: residual, Rayleigh shift,
                            // next-vector dot (non-negative: atomicMax on the bits)
   long long tc_pair_tiles; // 128 x 128 x 32 BF16 slice-pair products the split GEMM issues
+  long long asm_fp64_cols; // mixed mode: columns of W whose entries were formed in FP64
 };
 
 // Public status of a finished update from its device status block (shared by
@@ -101,6 +102,9 @@ struct Sub {
   // lam' as (hi, lo) float pairs, U' as K float arrays of ld.
   const float2* lamf = nullptr;
   const float* Usf = nullptr;
+  // Mixed mode with vectors: U' - Usf rounded to FP32 (U' = Usf + Ulo to 2^-48
+  // relative), for the double-float eq. (10) entries of the assembly; or null.
+  const float* Ulo = nullptr;
   // Products u_ia u_ib (a <= b, row-major over the upper triangle) of every
   // kept row, K(K+1)/2 arrays of ld doubles (null: form them from Us).  The
   // zero finder's FP64 sums then take M^_ab += r_i (u_ia u_ib) without the K
@@ -176,6 +180,97 @@ __device__ __forceinline__ void tc_split_scaled(double x, double s, __nv_bfloat1
   tc_split_prescaled(x, s * 1099511627776.0, out);
 }
 
+// ---- double-float arithmetic (pairs of FP32) ---------------------------------
+// A value h + l with |l| <= ulp(h) / 2: 48 significant bits on the FP32 pipe,
+// whose rate on this part is 64 times the FP64 pipe's.  Error-free transforms
+// after Knuth (two-sum) and the FMA product; the products and quotients below
+// carry relative errors of a few units of 2^-48.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return DF{s, (a - (s - bb)) + (b - bb)};
+}
+// h + l renormalised when |h| >= |l| (or h = 0).
+__device__ __forceinline__ DF df_fast(float h, float l) {
+  const float s = h + l;
+  return DF{s, l - (s - h)};
+}
+// x as a pair from the bits of x, with no FP64 arithmetic and no FP64/FP32
+// conversion (those take many FP64-pipe cycles on this part): h = x
+// truncated to 24 significant bits, l = the other 29 fraction bits rounded to
+// 24.  Zero and |x| in [2^-60, 2^60) return true; other x (tiny, huge, Inf,
+// NaN) return false and a zero pair.
+__device__ __forceinline__ bool df_bits(double x, DF& out) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+  const unsigned sign = hi & 0x80000000u;
+  if (ex < -60 || ex > 59) {
+    out = DF{0.0f, 0.0f};
+    return (b << 1) == 0ull;
+  }
+  const float h = __uint_as_float(sign | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const unsigned r = (unsigned)(b & 0x1fffffffu);
+  // r < 2^29 as r_hi 2^16 + r_lo, both exact in FP32 (2^23 + v - 2^23)
+  const float rh = __uint_as_float(0x4b000000u | (r >> 16)) - 8388608.0f;
+  const float rl = __uint_as_float(0x4b000000u | (r & 0xffffu)) - 8388608.0f;
+  const float l = fmaf(rh, 65536.0f, rl) * __uint_as_float((unsigned)(ex - 52 + 127) << 23);
+  out = DF{h, sign ? -l : l};
+  return true;
+}
+// An FP32 value as FP64 from its bits (normal or zero input; subnormals give 0).
+__device__ __forceinline__ double d_of_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast(p, e);
+}
+// 1 / d from an FP32 seed and one Newton step carried in the pair:
+// r = r0 (1 + e + e^2), e = 1 - d r0 (|e| <= 2^-22).
+__device__ __forceinline__ DF df_rcp(DF d) {
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(d.h));
+  float e = fmaf(-d.h, r0, 1.0f);
+  e = fmaf(-d.l, r0, e);
+  const float re = r0 * e;
+  return df_fast(r0, fmaf(re, e, re));
+}
+
+// The five digits of tc_split_prescaled from a pair y = h + l, |y| < 2^39:
+// digits are peeled from the top (q = rint(h / 2^(8j)), h -= q 2^(8j), exact),
+// the pair renormalised after each step so that h carries the rounded value.
+// The digits sum to rint(y) up to the last place; |m_p| <= 129 (exact in
+// BF16, and within the exact-accumulation bound of the GEMM).
+__device__ __forceinline__ void tc_split_df(DF y, __nv_bfloat16 (&out)[kTcSlices]) {
+  float h = y.h, l = y.l;
+  float m[kTcSlices];
+#pragma unroll
+  for (int p = 0; p < kTcSlices - 1; ++p) {
+    const float unit = __int_as_float((127 + 8 * (kTcSlices - 1 - p)) << 23);  // 2^(8(4-p))
+    const float q = rintf(h * __int_as_float((127 - 8 * (kTcSlices - 1 - p)) << 23));
+    h = fmaf(-q, unit, h);
+    const DF r = df_two_sum(h, l);
+    h = r.h;
+    l = r.l;
+    m[p] = q;
+  }
+  m[kTcSlices - 1] = rintf(h + l);
+#pragma unroll
+  for (int p = 0; p < kTcSlices; ++p) out[p] = __float2bfloat16_rn(ldexpf(m[p], -8 * p));
+}
+
 __device__ __forceinline__ void tc_split(double r, __nv_bfloat16 (&out)[kTcSlices]) {
   tc_split_scaled(r, 1.0, out);
 }
@@ -232,6 +327,7 @@ struct ProbDesc {
   DevStatus* st;
   float2* lamf;            // mixed mode: FP32 copies for the coarse zero-finder phase
   float* Usf;
+  float* Ulo;              // mixed mode with vectors: low parts of U' (see Sub)
   double* Vr;              // reflectors of the runs of equal lam (n x k), see runs.cu
   double* taur;            // their scalars (n)
   int* runs;               // (g0, m) pairs (n ints)
@@ -253,6 +349,7 @@ __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
   s.negmask = d.negmask;
   s.lamf = d.lamf;
   s.Usf = d.Usf;
+  s.Ulo = d.Ulo;
   s.Pp = d.Pp;
   return s;
 }

@@ -1702,6 +1702,23 @@ __global__ void deflated_kernel(Sub sub, int64_t n, const int* __restrict__ idx_
 
 constexpr int kAsmThreads = 256;
 constexpr int kAsmCache = 32;
+// Dynamic shared memory of the assembly kernels: one column's entries (n' <=
+// kAsmThreads * kAsmCache), kept between the norm pass and the writing pass
+// (in shared memory, not registers, so that several CTAs share an SM).
+constexpr size_t kAsmSmem = sizeof(double) * kAsmThreads * kAsmCache;
+// Once per kernel and device (the attribute outlives the launch).
+template <typename Kern>
+cudaError_t allow_asm_smem(Kern* k) {
+  static unsigned long long done = 0ull;  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsmSmem);
+  if (e == cudaSuccess) __atomic_fetch_or(&done, bit, __ATOMIC_RELEASE);
+  return e;
+}
 
 // Sum over the CTA of one value per thread (every thread gets the sum); sh
 // holds kAsmThreads / 32 doubles and may be reused right after.
@@ -1729,8 +1746,8 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
                                               const double* __restrict__ mu_sec,
                                               double* __restrict__ lam_out, double* __restrict__ W,
                                               const WSlices& ws, int m, double* s_n2, double* s_mx,
-                                              int* s_ix, int64_t pos_shift = 0, double* errs = nullptr,
-                                              DevStatus* stw = nullptr) {
+                                              int* s_ix, double* s_w, int64_t pos_shift = 0,
+                                              double* errs = nullptr, DevStatus* stw = nullptr) {
   const int t = threadIdx.x;
   const double mu = mu_sec[m];
   const int64_t pos = m + lower_bound_d(lam_defl, nd, mu) - pos_shift;
@@ -1756,7 +1773,122 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
   // Up to kAsmCache entries per thread are kept in registers for the writing
   // pass (n' <= kAsmThreads * kAsmCache); larger columns are recomputed.
   const bool cached = nk <= kAsmThreads * kAsmCache;
-  double wc[kAsmCache];
+  if (!W && ws.Ws != nullptr && sub.Ulo != nullptr && errs == nullptr && cached) {
+    // Mixed mode: the eq. (10) entries in double-float arithmetic.  W feeds a
+    // split that keeps 2^-40 of each column's largest entry, so a few units of
+    // 2^-48 per entry suffice; only d_i = (lam_i - lam_o) - tau is formed in
+    // FP64 (next to the root its two terms cancel).  alpha is scaled by a
+    // power of 2, which the normalisation cancels.  A column whose values
+    // leave the FP32 range takes the FP64 path below.
+    double amax = 0.0;
+#pragma unroll
+    for (int c = 0; c < K; ++c) amax = fmax(amax, fabs(al[c]));
+    const double fro2 = sub.st->fro2;
+    if (amax > 0x1p-100 && amax < 0x1p100 && fro2 > 0x1p-100 && fro2 < 0x1p100) {  // uniform
+      int ea;
+      frexp(amax, &ea);
+      const double sa = ldexp(1.0, -ea);
+      DF a[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) df_bits(al[c] * sa, a[c]);  // |.| < 1; below 2^-60 flushes to 0
+      DF wa_d, wb_d;
+      bool good = df_bits(wa * sa, wa_d) && df_bits(wb * sa, wb_d);
+      float2* const wd = reinterpret_cast<float2*>(s_w);  // this thread's entries only
+      float n2h = 0.0f, n2l = 0.0f;
+      DF mxd = DF{-1.0f, 0.0f};
+      int ixd = 0x7fffffff;
+#pragma unroll
+      for (int c = 0; c < kAsmCache; ++c) {
+        const int i = t + c * kAsmThreads;
+        DF w = DF{0.0f, 0.0f};
+        if (i < nk) {
+          if (i == ia) {
+            w = wa_d;
+          } else if (i == ib) {
+            w = wb_d;
+          } else {
+            // u_i^T alpha: exact FP32 products, two-sum accumulation
+            float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+            for (int cc = 0; cc < K; ++cc) {
+              const float uh = __ldg(sub.Usf + (size_t)cc * sub.ld + i);
+              const float ul = __ldg(sub.Ulo + (size_t)cc * sub.ld + i);
+              const float pr = uh * a[cc].h;
+              float e = fmaf(uh, a[cc].h, -pr);
+              e = fmaf(uh, a[cc].l, e);
+              e = fmaf(ul, a[cc].h, e);
+              const DF sm = df_two_sum(sh, pr);
+              sh = sm.h;
+              sl += sm.l + e;
+            }
+            DF d;
+            good = df_bits((sub.lam[i] - lam_o) - tau, d) && d.h != 0.0f && good;
+            w = df_mul(df_two_sum(sh, sl), df_rcp(d));
+          }
+          good = good && fabsf(w.h) <= 0x1p100f;  // false for NaN
+          const float pr = w.h * w.h;
+          const float e = fmaf(2.0f * w.h, w.l, fmaf(w.h, w.h, -pr));
+          const DF sm = df_two_sum(n2h, pr);
+          n2h = sm.h;
+          n2l += sm.l + e;
+          // largest |w| (the first index on ties), compared as pairs
+          const float mh = fabsf(w.h), ml = w.h < 0.0f ? -w.l : w.l;
+          if (mh > mxd.h || (mh == mxd.h && ml > mxd.l)) {
+            mxd = DF{mh, ml};
+            ixd = i;
+          }
+          wd[i] = make_float2(w.h, w.l);
+        }
+      }
+      if (!__syncthreads_or(!good)) {
+        s_n2[t] = d_of_bits(n2h) + d_of_bits(n2l);
+        s_mx[t] = d_of_bits(mxd.h) + d_of_bits(mxd.l);
+        s_ix[t] = ixd;
+        __syncthreads();
+        for (int s = kAsmThreads / 2; s > 0; s >>= 1) {
+          if (t < s) {
+            s_n2[t] += s_n2[t + s];
+            const double om = s_mx[t + s];
+            const int oi = s_ix[t + s];
+            if (om > s_mx[t] || (om == s_mx[t] && oi < s_ix[t])) {
+              s_mx[t] = om;
+              s_ix[t] = oi;
+            }
+          }
+          __syncthreads();
+        }
+        const double nrm = sqrt(s_n2[0]);
+        const int imax = (s_ix[0] >= 0 && s_ix[0] < nk) ? s_ix[0] : 0;
+        __syncthreads();
+        // sign and exponent from the FP64 value of the largest entry, formed once
+        if (t == 0) s_mx[0] = wcomp(imax) * sa;
+        __syncthreads();
+        const double wmax = s_mx[0];
+        const double scale = (wmax < 0.0 ? -1.0 : 1.0) / nrm;
+        const int f = tc_scale_exp(fabs(wmax * scale));
+        DF sd;
+        if (df_bits(ldexp(scale, 40 - f), sd) && sd.h != 0.0f) {  // uniform
+          if (t == 0) ws.fcol[pos] = f;
+          __nv_bfloat16* col = ws.Ws + (size_t)pos * ws.lds;
+#pragma unroll
+          for (int c = 0; c < kAsmCache; ++c) {
+            const int i = t + c * kAsmThreads;
+            if (i < nk) {
+              __nv_bfloat16 dg[kTcSlices];
+              const float2 wv = wd[i];
+              tc_split_df(df_mul(DF{wv.x, wv.y}, sd), dg);
+              const int j = sub.idx[i];
+#pragma unroll
+              for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = dg[q];
+            }
+          }
+          return;
+        }
+      }
+      __syncthreads();  // the reduction arrays are reused by the FP64 path
+    }
+  }
+  if (!W && stw && t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&stw->asm_fp64_cols), 1ull);
   double n2 = 0.0, mx = -1.0;
   int ix = 0x7fffffff;
   if (cached) {
@@ -1764,7 +1896,7 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
     for (int c = 0; c < kAsmCache; ++c) {
       const int i = t + c * kAsmThreads;
       const double w = (i < nk) ? wcomp(i) : 0.0;
-      wc[c] = w;
+      if (i < nk) s_w[i] = w;
       n2 = fma(w, w, n2);
       if (i < nk && fabs(w) > mx) {
         mx = fabs(w);
@@ -1814,7 +1946,7 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
 #pragma unroll
         for (int c = 0; c < kAsmCache; ++c) {
           const int i = t + c * kAsmThreads;
-          if (i < nk) f(i, wc[c] * scale);
+          if (i < nk) f(i, s_w[i] * scale);
         }
       } else {
         for (int i = t; i < nk; i += kAsmThreads) f(i, wcomp(i) * scale);
@@ -1891,7 +2023,7 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
 #pragma unroll
       for (int c = 0; c < kAsmCache; ++c) {
         const int i = t + c * kAsmThreads;
-        if (i < nk) col[sub.idx[i]] = wc[c] * scale;
+        if (i < nk) col[sub.idx[i]] = s_w[i] * scale;
       }
     } else {
       for (int i = t; i < nk; i += kAsmThreads) col[sub.idx[i]] = wcomp(i) * scale;
@@ -1908,7 +2040,7 @@ __device__ __forceinline__ void assemble_root(const Sub& sub, const RootOut& roo
         const int i = t + c * kAsmThreads;
         if (i < nk) {
           __nv_bfloat16 d[kTcSlices];
-          tc_split_prescaled(wc[c], s2, d);
+          tc_split_prescaled(s_w[i], s2, d);
           const int j = sub.idx[i];
 #pragma unroll
           for (int q = 0; q < kTcSlices; ++q) col[(size_t)q * ws.plane + j] = d[q];
@@ -1934,11 +2066,12 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_kernel(
   __shared__ double s_n2[kAsmThreads];
   __shared__ double s_mx[kAsmThreads];
   __shared__ int s_ix[kAsmThreads];
+  extern __shared__ __align__(16) double s_w[];
   if (input_invalid(st)) return;
   const int nk = *sub.n_dev;
   const int nd = st->n_defl;
   for (int m = blockIdx.x; m < nk; m += gridDim.x) {
-    assemble_root<K>(sub, roots, n, lam_defl, nd, nk, mu_sec, lam_out, W, ws, m, s_n2, s_mx, s_ix);
+    assemble_root<K>(sub, roots, n, lam_defl, nd, nk, mu_sec, lam_out, W, ws, m, s_n2, s_mx, s_ix, s_w);
     __syncthreads();
   }
 }
@@ -1968,12 +2101,13 @@ __device__ __forceinline__ WSlices wslices_of(const ProbDesc& d, bool mixed) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(kAsmThreads) assemble_grouped_kernel(const ProbDesc* __restrict__ P,
+__global__ void __launch_bounds__(kAsmThreads, 2) assemble_grouped_kernel(const ProbDesc* __restrict__ P,
                                                                        ClassDesc c, bool vectors,
                                                                        bool mixed) {
   __shared__ double s_n2[kAsmThreads];
   __shared__ double s_mx[kAsmThreads];
   __shared__ int s_ix[kAsmThreads];
+  extern __shared__ __align__(16) double s_w[];
   const int total = c.pk[c.count];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int p = find_owner(c.pk, c.count, item);
@@ -1982,7 +2116,7 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_grouped_kernel(const Pro
     const Sub sub = sub_of(d);
     const WSlices ws = wslices_of(d, vectors && mixed);
     assemble_root<K>(sub, rootout_of(d), d.n, d.lam_defl, d.st->n_defl, *sub.n_dev, d.mu_sec, d.lam,
-                     (vectors && !mixed) ? d.W : nullptr, ws, item - c.pk[p], s_n2, s_mx, s_ix, 0,
+                     (vectors && !mixed) ? d.W : nullptr, ws, item - c.pk[p], s_n2, s_mx, s_ix, s_w, 0,
                      vectors ? d.errors : nullptr, d.st);
     __syncthreads();
   }
@@ -2116,10 +2250,11 @@ __global__ void __launch_bounds__(kAsmThreads) assemble_select_kernel(
   __shared__ double s_n2[kAsmThreads];
   __shared__ double s_mx[kAsmThreads];
   __shared__ int s_ix[kAsmThreads];
+  extern __shared__ __align__(16) double s_w[];
   const int nk = *sub.n_dev;
   for (int m = r0 + blockIdx.x; m < r1; m += gridDim.x) {
     assemble_root<K>(sub, roots, n, lam_dsel, dsel, nk, mu_sec, mu_out, W, WSlices(), m, s_n2, s_mx, s_ix,
-                     r0);
+                     s_w, r0);
     __syncthreads();
   }
 }
@@ -2144,7 +2279,9 @@ cudaError_t launch_assemble_select_k(const Sub& sub, const RootOut& roots, int64
   const int cnt = r1 - r0;
   if (cnt > 0) {
     mu_select_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(sub, roots, r0, r1, mu_sec);
-    assemble_select_kernel<K><<<cnt < 65535 ? cnt : 65535, kAsmThreads, 0, s>>>(
+    const cudaError_t e = allow_asm_smem(assemble_select_kernel<K>);
+    if (e != cudaSuccess) return e;
+    assemble_select_kernel<K><<<cnt < 65535 ? cnt : 65535, kAsmThreads, kAsmSmem, s>>>(
         sub, roots, n, lam_defl + dlo, dsel, r0, r1, mu_sec, mu_out, W);
   }
   if (dsel > 0)
@@ -2194,7 +2331,9 @@ cudaError_t launch_assemble_k(const Sub& sub, const RootOut& roots, int64_t n,
   const int ld = sub.ld;
   mu_kernel<<<(ld + 255) / 256, 256, 0, s>>>(sub, roots, mu_sec);
   int blocks = ld < 65535 ? ld : 65535;
-  assemble_kernel<K><<<blocks, kAsmThreads, 0, s>>>(sub, roots, n, lam_defl, st, mu_sec, lam_out, W,
+  const cudaError_t e = allow_asm_smem(assemble_kernel<K>);
+  if (e != cudaSuccess) return e;
+  assemble_kernel<K><<<blocks, kAsmThreads, kAsmSmem, s>>>(sub, roots, n, lam_defl, st, mu_sec, lam_out, W,
                                                      ws);
   int nb = (int)((n + 255) / 256);
   if (nb > 4096) nb = 4096;
@@ -2257,7 +2396,9 @@ cudaError_t assemble_grouped_k(const ProbDesc* P, const ClassDesc& c, int max_it
   const int mb = max_items > 0 ? (max_items + 255) / 256 : 1;
   mu_grouped_kernel<<<mb < 4096 ? mb : 4096, 256, 0, s>>>(P, c);
   const int ab = max_items > 0 ? (max_items < 65535 ? max_items : 65535) : 1;
-  assemble_grouped_kernel<K><<<ab, kAsmThreads, 0, s>>>(P, c, vectors, mixed);
+  const cudaError_t e = allow_asm_smem(assemble_grouped_kernel<K>);
+  if (e != cudaSuccess) return e;
+  assemble_grouped_kernel<K><<<ab, kAsmThreads, kAsmSmem, s>>>(P, c, vectors, mixed);
   const int db = max_defl > 0 ? (max_defl + 255) / 256 : 1;
   deflated_grouped_kernel<<<db < 4096 ? db : 4096, 256, 0, s>>>(P, c, vectors, mixed);
   return cudaGetLastError();

@@ -86,6 +86,8 @@ def test_pair_errors_match_oracle(eu, handles, mode, n, k, sigma, kind):
         assert np.max(np.abs(mu64 - mu)) <= 1e-13 * normA
         gemm = 2.0 * _gemm_err(X, X64) + 1e-13
         assert np.max(_gemm_err(X, X64)) <= 1e-9
+        # the report needs the FP64 entries: every secular column takes that path
+        assert rep["asm_fp64_cols"] == n - rep["n_deflated"]
     assert np.all(np.abs(res - E[:, 0]) <= gemm), np.max(np.abs(res - E[:, 0]) - gemm)
     # (1) Rayleigh quotient of the FP64 vector agrees with mu
     assert np.max(E[:, 1]) <= 1e-13

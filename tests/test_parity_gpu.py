@@ -320,6 +320,7 @@ def test_mixed_gemm_pair_products_issued(eu, handle, handle_mixed):
     assert rc == 0
     full = _pair_products_full(2100)
     assert 6 * full // 15 <= rep["tc_pair_tiles"] <= full
+    assert rep["asm_fp64_cols"] == 0  # every column of W from the double-float path
     _check_full(P, mu, X)
     # no split GEMM: FP64 mode, eigenvalues only
     rc, rep, _, _ = _run_update(eu, handle, P)
