@@ -221,14 +221,23 @@ __device__ __forceinline__ bool df_bits(double x, DF& out) {
   out = DF{h, sign ? -l : l};
   return true;
 }
-// An FP32 value as FP64 from its bits (normal or zero input; subnormals give 0).
+// An FP32 value as FP64 from its bits, exactly (zero, subnormal, Inf and NaN
+// included), without the conversion's FP64-pipe cycles.
 __device__ __forceinline__ double d_of_bits(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u) return 0.0;
-  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
-                                          ((unsigned long long)(e + 896u) << 52) |
-                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned e = (u >> 23) & 0xffu;
+  unsigned m = u & 0x7fffffu;
+  if (e == 0u) {
+    if (m == 0u) return __longlong_as_double((long long)sign);
+    const int sh = __clz(m) - 8;  // normalise: leading one to bit 23
+    m = (m << sh) & 0x7fffffu;
+    e = 1u - (unsigned)sh;        // as a biased FP32 exponent (may wrap below 1)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)m << 29)));
+  }
+  const unsigned long long de = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)m << 29)));
 }
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
   const float p = a.h * b.h;
