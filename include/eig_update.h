@@ -174,6 +174,11 @@ typedef struct {
                                8192 rows, and those whose values leave the
                                double-float range (magnitudes outside
                                [2^-60, 2^60]).  0 otherwise. */
+  int64_t gj32_total;       /* EIG_MIXED: certified FP32 evaluations whose k x k
+                               step was a Gauss-Jordan inverse of the bordered
+                               matrix (one root in the bracket: the count from
+                               the sign of its determinant); the other counted
+                               FP32 evaluations took its eigen-decomposition. */
 } eig_report;
 
 /* ---- lifetime ----------------------------------------------------------- */

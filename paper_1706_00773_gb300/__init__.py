@@ -89,7 +89,7 @@ class eig_report(ctypes.Structure):
                 ("redo32_total", ctypes.c_int64), ("taylor_total", ctypes.c_int64),
                 ("max_pair_residual", ctypes.c_double), ("max_pair_rayleigh", ctypes.c_double),
                 ("max_pair_orth", ctypes.c_double), ("tc_pair_tiles", ctypes.c_int64),
-                ("asm_fp64_cols", ctypes.c_int64)]
+                ("asm_fp64_cols", ctypes.c_int64), ("gj32_total", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -769,6 +769,7 @@ void fill_report(eig_report* rep, const eig_problem* P, const DevStatus& st, con
   rep->iters_total = st.iters_total;
   rep->iters32_total = st.iters32_total;
   rep->redo32_total = st.redo32_total;
+  rep->gj32_total = st.gj32_total;
   rep->taylor_total = st.taylor_total;
   rep->n_runs = st.n_runs;
   rep->iters_max = st.iters_max;

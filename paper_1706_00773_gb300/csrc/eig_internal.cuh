@@ -47,6 +47,7 @@ struct DevStatus {
   double hi_sent;
   long long iters32_total; // FP32 (coarse-phase) evaluations
   long long redo32_total;  // FP32 evaluations whose count was not certified
+  long long gj32_total;    // certified FP32 evaluations whose k x k step was a Gauss-Jordan inverse
   long long taylor_total;  // evaluations by a first-order update of the K x K sums
   int n_runs;              // runs of exactly repeated lam rotated before deflation
   int run_rows;            // rows in those runs

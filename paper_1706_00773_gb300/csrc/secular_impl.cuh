@@ -1062,7 +1062,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
   const double* __restrict__ lam = sub.lam;
   const double* __restrict__ Us = sub.Us;
   // ---- placement (warp 0 of the group; every lane holds the same state) ----
-  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, it32 = 0, itay = 0, slow = 0, ia = -1, ib = -1;
+  int o = 0, p = 0, c_lo = 0, c_hi = 0, it = 0, it32 = 0, itay = 0, itgj = 0, slow = 0, ia = -1, ib = -1;
   // Coarse phase in FP32 (mixed mode): steps from FP32 sums, the bracket moved
   // only by counts that the error bound certifies; then FP64 to the end.
   bool phase32 = (sub.lamf != nullptr);
@@ -1365,6 +1365,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
       ++it;
       if (ph32) ++it32;
       if (tay) ++itay;
+      if (gj) ++itgj;
       const double wprev = th - tl;
       if (count <= m) {
         tl = tau;
@@ -1564,6 +1565,7 @@ __device__ __forceinline__ void root_solve(const Sub& sub, const int* __restrict
           atomicAdd((unsigned long long*)&st->iters_total, (unsigned long long)(it - it32 - itay));
           if (itay) atomicAdd((unsigned long long*)&st->taylor_total, (unsigned long long)itay);
           if (it32) atomicAdd((unsigned long long*)&st->iters32_total, (unsigned long long)it32);
+          if (itgj) atomicAdd((unsigned long long*)&st->gj32_total, (unsigned long long)itgj);
           atomicMax(&st->iters_max, it);
           if (notconv) {
             atomicAdd((unsigned long long*)&st->n_notconv, 1ull);

@@ -287,6 +287,7 @@ def test_mixed_matches_fp64_and_oracle(eu, handle, handle_mixed, n, k, sigma):
     assert np.max(np.abs(mum - mu64)) <= 1e-13 * norm2_A(P["lam"], P["K"])
     if n > 1:
         assert rep["iters32_total"] > 0
+    assert 0 <= rep["gj32_total"] <= rep["iters32_total"]
     # X from the tensor cores vs the FP64 GEMM: 5 slices keep ~2^-40 of the scale
     assert np.max(np.abs(Xm - X64)) <= 1e-10
     _check_full(P, mum, Xm)
