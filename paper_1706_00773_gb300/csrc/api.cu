@@ -461,6 +461,11 @@ Table layout_table(eig_ctx* h, const std::vector<TableItem>& items, char* base, 
                                   : nullptr;
     if (d.errors) T.any_errors = true;
     if (n > T.max_n) T.max_n = n;
+    if (mixed) {  // K split for the double-float projection
+      d.Kh = reinterpret_cast<float*>(b.take(sizeof(float) * (size_t)n * k));
+      d.Kl = reinterpret_cast<float*>(b.take(sizeof(float) * (size_t)n * k));
+      d.Kexp = reinterpret_cast<int*>(b.take(sizeof(int) * 16));
+    }
     if (mixed) {  // FP32 copies for the coarse phase of the zero finder
       d.lamf = reinterpret_cast<float2*>(b.take(sizeof(float2) * ld));
       d.Usf = reinterpret_cast<float*>(b.take(sizeof(float) * ld * K));
@@ -545,9 +550,9 @@ int enqueue_table(eig_ctx* h, const Table& T, int count, bool vectors, bool mixe
   MARK(0);
   CK(cudaMemcpyAsync(T.d_desc, img.data(), img.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(T.d_st, 0, sizeof(DevStatus) * count, s));
-  CK(launch_project_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
+  CK(launch_project_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s, mixed));
   CK(launch_runs_qr_grouped(T.d_desc, count, T.max_n, s));
-  nl += 2;
+  nl += mixed ? 3 : 2;
   MARK(1);
   CK(launch_deflate_grouped(T.d_desc, count, s));
   CK(launch_products_grouped(T.d_desc, count, T.d_colpre, T.total_cols, s));
@@ -1474,7 +1479,9 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
   const size_t ws_bytes = tc ? align_up(2 * (size_t)tc_num_slices() * (size_t)tc_slice_ld((int)n) * capc, 256) : 0;
   const size_t aux_bytes = tc ? align_up(8 * (size_t)n, 256) + align_up(4 * (size_t)n, 256) + align_up(4 * capc, 256) : 0;
   const size_t pp_bytes = align_up(sizeof(double) * (size_t)ld * (size_t)(Kp * (Kp + 1) / 2), 256);
-  const size_t need = base + 256 + f32_bytes + wsel_bytes + qs_bytes + ws_bytes + aux_bytes + pp_bytes;
+  // mixed mode: K split for the double-float projection (as the full update's)
+  const size_t ksplit_bytes = mixed ? 2 * align_up(sizeof(float) * (size_t)n * k, 256) + 256 : 0;
+  const size_t need = base + 256 + f32_bytes + wsel_bytes + qs_bytes + ws_bytes + aux_bytes + pp_bytes + ksplit_bytes;
   int rc = ensure_ws(h, need);
   if (rc) return rc;
   Carve c = plan(h->ws, n, k, false, false, false);
@@ -1493,10 +1500,18 @@ int eig_update_select(eig_handle h, int64_t n, int32_t k, const double* Q, const
                  : nullptr;
   // products of the kept rows, as the update's zero finder takes them
   double* Pp = reinterpret_cast<double*>(tcb + qs_bytes + ws_bytes + aux_bytes);
+  char* ksb = tcb + qs_bytes + ws_bytes + aux_bytes + pp_bytes;
+  float* Kh = mixed ? reinterpret_cast<float*>(ksb) : nullptr;
+  float* Kl = mixed ? reinterpret_cast<float*>(ksb + align_up(sizeof(float) * (size_t)n * k, 256)) : nullptr;
+  int* Kexp = mixed ? reinterpret_cast<int*>(ksb + 2 * align_up(sizeof(float) * (size_t)n * k, 256)) : nullptr;
   const double xv[2] = {vl, vu};
   CK(cudaMemsetAsync(c.st, 0, sizeof(DevStatus), s));
   CK(cudaMemcpyAsync(pts, xv, sizeof(xv), cudaMemcpyHostToDevice, s));
-  CK(launch_project_f64(n, k, Q, K, c.U, s));
+  // the full update's projection in either mode, so that the roots agree bit for bit
+  if (mixed)
+    CK(launch_project_mixed(n, k, Q, K, c.U, Kh, Kl, Kexp, s));
+  else
+    CK(launch_project_f64(n, k, Q, K, c.U, s));
   CK(launch_runs_qr(n, k, lambda, c.U, c.Vr, c.taur, c.runs, c.st, s));
   CK(launch_deflate(n, k, Kp, lambda, c.U, negmask, c.lam_keep, c.Us, ld, c.idx_keep, c.idx_defl,
                     c.lam_defl, c.st, s, lamf, Usf));

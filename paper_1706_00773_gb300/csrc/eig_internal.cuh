@@ -344,6 +344,9 @@ struct ProbDesc {
   double* errors;          // caller: n x 4 per-eigenpair report (column-major), or null
   double* Pp;              // products u_ia u_ib of the kept rows, K(K+1)/2 arrays of ld (see Sub)
   unsigned* wnz;           // mixed mode: non-zero map of W's two leading slices (see WSlices)
+  float* Kh;               // mixed mode: K's columns scaled by 2^-Kexp[c], FP32 high parts (n x k)
+  float* Kl;               // and low parts
+  int* Kexp;               // per column of K (16 entries)
 };
 
 __host__ __device__ inline Sub sub_of(const ProbDesc& d) {
@@ -415,8 +418,14 @@ cudaError_t launch_project_f64(int64_t n, int k, const double* Q, const double* 
                                cudaStream_t s);
 // U = Q^T K for every update of the table; col_prefix (device, count+1): prefix
 // sums of n over the table.
+// U = Q^T K of one update in double-float arithmetic (as the mixed-mode table
+// forms it): Kh, Kl n x k floats, Kexp k ints of scratch.
+cudaError_t launch_project_mixed(int64_t n, int k, const double* Q, const double* K, double* U, float* Kh,
+                                 float* Kl, int* Kexp, cudaStream_t s);
+// mixed: U in double-float arithmetic (K split by a kernel first; ProbDesc::Kh,
+// Kl, Kexp), a column with values outside that range in FP64.
 cudaError_t launch_project_grouped(const ProbDesc* P, int count, const long long* col_prefix,
-                                   long long total_cols, cudaStream_t s);
+                                   long long total_cols, cudaStream_t s, bool mixed = false);
 // Deflation + compaction for every update (one CTA each); also keeps lam_old.
 cudaError_t launch_deflate_grouped(const ProbDesc* P, int count, cudaStream_t s);
 // Products u_ia u_ib of the kept rows into ProbDesc::Pp (updates with Pp set);

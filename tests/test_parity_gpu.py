@@ -330,6 +330,38 @@ def test_mixed_gemm_pair_products_issued(eu, handle, handle_mixed):
     assert rc == 0 and rep["tc_pair_tiles"] == 0
 
 
+def test_mixed_projection_fallbacks(eu, handle, handle_mixed):
+    """Mixed mode forms U = Q^T K in double-float arithmetic (pairs of FP32,
+    K's columns scaled by powers of 2).  A K whose row 17 is 2^20 times the
+    others (a wide dynamic range in every column of U) still gives the
+    eigenvalues of diag(lam) + U Sigma U^T to 1e-13 |A| (numpy's symmetric
+    eigensolver as the reference).  A column of Q holding an Inf or a NaN takes
+    the FP64 projection, so the non-finite input reaches the deflation check
+    (EIG_EINVAL) instead of being flushed; a non-finite K likewise."""
+    P = workloads.general(600, 5, seed=91, sigma="mixed", lam_kind="uniform")
+    K = P["K"].copy()
+    K[17, :] *= 2.0 ** 20
+    U = P["Q"].T @ K
+    ref = np.linalg.eigvalsh(np.diag(P["lam"]) + (U * P["sigma"].astype(float)) @ U.T)
+    normA = np.max(np.abs(P["lam"])) + np.sum(U * U)
+    for h in (handle, handle_mixed):
+        rc, rep, mu, _ = _run_update(eu, h, dict(P, K=K), want=eu.EIG_VALUES | eu.EIG_REPORT)
+        assert rc == 0
+        assert np.max(np.abs(mu - ref)) <= 1e-13 * normA
+    for bad in ("Q_inf", "Q_nan", "K_nan"):
+        Pn = dict(P, Q=P["Q"].copy(), K=P["K"].copy())
+        if bad == "Q_inf":
+            Pn["Q"][5, 9] = np.inf
+        elif bad == "Q_nan":
+            Pn["Q"][5, 9] = np.nan
+        else:
+            Pn["K"][40, 2] = np.nan
+        rc, _ = eu.eig_update_rank_k(handle_mixed, dev_colmajor(Pn["Q"]), dev_vec(Pn["lam"]),
+                                     dev_colmajor(Pn["K"]), Pn["sigma"], eu.EIG_VALUES | eu.EIG_VECTORS,
+                                     raise_on_error=False)
+        assert rc == eu.EIG_EINVAL, bad
+
+
 def test_mixed_full_size_sampled(eu, handle_mixed):
     P = workloads.general_rank_k(k=8, seed=2000, n=8192, device="cuda:0")
     rc, rep, mu, X = _run_update(eu, handle_mixed, P)
