@@ -56,9 +56,14 @@ extern "C" {
 
 /* ---- precision modes (eig_init_params.mode) ----------------------------- */
 #define EIG_FP64 0u  /* every step in FP64 on the CUDA cores */
-#define EIG_MIXED 1u /* secular steps in FP64; X = Q W as split-BF16 products
-                        on the tensor cores with exact FP32 chunks and
-                        double-float accumulation */
+#define EIG_MIXED 1u /* U = Q^T K and the eq. (10) entries of W in
+                        double-float arithmetic (pairs of FP32, a few units
+                        of 2^-48; values outside that range in FP64); pole
+                        counts and the zero finder's coarse steps on FP32
+                        sums, taken only where an error bound certifies them,
+                        every root finished in FP64; X = Q W as split-BF16
+                        products on the tensor cores with exact FP32 chunks
+                        and double-float accumulation */
 
 /* ---- what to compute (eig_problem.want) --------------------------------- */
 #define EIG_VALUES 1u  /* eigenvalues into lambda */
