@@ -104,6 +104,18 @@ def test_pair_errors_match_oracle(eu, handles, mode, n, k, sigma, kind):
     assert rep["max_pair_orth"] == np.max(E[:, 3])
 
 
+@pytest.mark.parametrize("seed", [1001, 1002])
+def test_mixed_projection_keeps_planted_deflation(eu, handles, seed):
+    """Mixed mode forms U = Q^T K in double-float arithmetic; its error on the
+    planted rows (|u_i| ~ 1e-15) must stay below the deflation threshold, so
+    the same rows deflate as in FP64 mode."""
+    W = workloads.indefinite_rank2(seed=seed, n=4096)
+    K, s = oracle.rank2_perturbation(4096, W["j"], W["a"])
+    P = dict(Q=W["Q"], lam=W["lam"], K=K, sigma=s)
+    reps = {mode: _run(eu, h, P)[0] for mode, h in handles.items()}
+    assert reps["mixed"]["n_deflated"] == reps["fp64"]["n_deflated"] == len(W["planted"])
+
+
 def test_pair_errors_deflated_pairs(eu, handles):
     """Planted deflation (one-row-one-column workload, n = 4096): deflated pairs
     report the deflation bound |U|_F |u_i| / |A| <= 8 eps."""
