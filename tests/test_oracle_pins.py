@@ -305,3 +305,20 @@ def test_sampled_roots_match_full_solve():
     assert np.array_equal(part["pos"], sel)
     assert np.max(np.abs(part["mu"] - full["mu"][sel])) == 0.0
     assert np.max(np.abs(np.abs(part["X"]) - np.abs(full["X"][:, sel]))) <= 1e-13
+
+
+@pytest.mark.parametrize("seed,sigma", [(91, "mixed"), (92, "psd")])
+def test_update_with_a_spiked_perturbation_matches_lapack(seed, sigma):
+    """One row of K scaled by 2^61: every row of U carries a component 2^61
+    times the rest, and ||U||^2 is ~2^114 times the spread of lambda.  The
+    oracle's eigenvalues still match LAPACK's symmetric eigensolver on
+    diag(lam) + U Sigma U^T to 1e-14 of |A| = max|lam| + ||U||_F^2 (LAPACK's own
+    error is a few units of eps |A|)."""
+    P = workloads.general(600, 5, seed=seed, sigma=sigma, lam_kind="uniform")
+    K = P["K"].copy()
+    K[17, :] *= 2.0 ** 61
+    U = P["Q"].T @ K
+    ref = np.linalg.eigvalsh(np.diag(P["lam"]) + (U * P["sigma"].astype(float)) @ U.T)
+    normA = np.max(np.abs(P["lam"])) + np.sum(U * U)
+    r = oracle.update(P["Q"], P["lam"], K, P["sigma"], want_vectors=False)
+    assert np.max(np.abs(r["mu"] - ref)) <= 1e-14 * normA
